@@ -1,0 +1,173 @@
+"""Right-hand side, time stepping, projection, sources and receivers of the oracle.
+
+Test infrastructure only (see the package docstring).
+
+Time integrators
+----------------
+* Leapfrog (Sec. V: "classic leap-frog"), staggered E/H.  Reading for the
+  start: H is given at t = 0 and advanced half a step with the H equation,
+  H^{1/2} = H^0 + dt/2 L_H(E^0); then E^{n+1} = E^n + dt L_E(H^{n+1/2}),
+  H^{n+3/2} = H^{n+1/2} + dt L_H(E^{n+1}).  Needs a flux whose E equation
+  depends on H only (central).
+* Low-storage RK4, five stages, 2N storage (Carpenter & Kennedy 1994):
+  res = a_k res + dt L(u, t + c_k dt);  u = u + b_k res.
+
+Point dipole source: j = d delta(r - r_s) g(t), entering the E equation as
+-(j, phi)_T = -g(t) d . phi(r_s) in the element containing r_s, with the
+Gaussian-modulated sine g(t) = sin(2 pi f0 (t - t0)) exp(-(t - t0)^2 / (2 s^2)),
+s = 1/(2 pi bw).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .basis import tet_quadrature
+
+# Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage Runge-Kutta.
+LSRK4_A = (0.0,
+           -567301805773.0 / 1357537059087.0,
+           -2404267990393.0 / 2016746695238.0,
+           -3550918686646.0 / 2091501179385.0,
+           -1275806237668.0 / 842570457699.0)
+LSRK4_B = (1432997174477.0 / 9575080441755.0,
+           5161836677717.0 / 13612068292357.0,
+           1720146321549.0 / 2090206949498.0,
+           3134564353537.0 / 4481467310338.0,
+           2277821191437.0 / 14882151754819.0)
+LSRK4_C = (0.0,
+           1432997174477.0 / 9575080441755.0,
+           2526269341429.0 / 6820363962896.0,
+           2006345519317.0 / 3224310063776.0,
+           2802321613138.0 / 2924317926251.0)
+
+
+def source_time(t, f0, bw, t0):
+    s = 1.0 / (2.0 * math.pi * bw)
+    return math.sin(2.0 * math.pi * f0 * (t - t0)) * math.exp(-(t - t0) ** 2 / (2.0 * s * s))
+
+
+class Solver:
+    """Time stepper over an oracle Assembly with batch columns S.
+
+    sources: list (length S or empty) of None or dict(pos, dir, f0, bw, t0);
+    column s is driven by sources[s].
+    """
+
+    def __init__(self, asm, S=1, sources=None):
+        self.asm = asm
+        self.S = S
+        self.src = []
+        sources = sources or []
+        for s, rec in enumerate(sources):
+            if rec is None:
+                continue
+            T = asm.mesh.locate(np.asarray(rec["pos"], dtype=np.float64))
+            B = asm._basis_vectors(T, np.asarray(rec["pos"], dtype=np.float64)[None, :])[0]
+            w = np.asarray(rec["dir"], dtype=np.float64) @ B      # d . phi_{j,l}(r_s)
+            self.src.append((s, T, w, rec))
+
+    # -- conversion from the shared (K, S, 6, N) state convention ------------
+    def pack(self, u, aux=None):
+        a = self.asm
+        K, N, S = a.K, a.N, u.shape[1]
+        x = np.zeros((a.ndof, S))
+        x[:K * 3 * N] = u[:, :, 0:3, :].transpose(0, 2, 3, 1).reshape(K * 3 * N, S)
+        x[K * 3 * N:2 * K * 3 * N] = u[:, :, 3:6, :].transpose(0, 2, 3, 1).reshape(K * 3 * N, S)
+        if a.nblk == 4 and aux is not None:
+            x[2 * K * 3 * N:3 * K * 3 * N] = aux[:, :, 0:3, :].transpose(0, 2, 3, 1).reshape(-1, S)
+            x[3 * K * 3 * N:] = aux[:, :, 3:6, :].transpose(0, 2, 3, 1).reshape(-1, S)
+        return x
+
+    def unpack(self, y, nelem=None):
+        """Row-space vector -> (fields (R, S, 6, N), aux or None)."""
+        a = self.asm
+        R = a.R if nelem is None else nelem
+        N, S = a.N, y.shape[1]
+        blocks = [y[b * R * 3 * N:(b + 1) * R * 3 * N].reshape(R, 3, N, S).transpose(0, 3, 1, 2)
+                  for b in range(a.nblk)]
+        u = np.concatenate(blocks[:2], axis=2)
+        aux = np.concatenate(blocks[2:], axis=2) if a.nblk == 4 else None
+        return u, aux
+
+    # -- operator --------------------------------------------------------------
+    def source_vector(self, t):
+        a = self.asm
+        f = np.zeros((a.Kmat.shape[0], self.S))
+        for s, T, w, rec in self.src:
+            if a.pos[T] < 0:
+                continue
+            g = source_time(t, rec["f0"], rec["bw"], rec["t0"])
+            r0 = a.pos[T] * a.n3
+            f[r0:r0 + a.n3, s] -= g * w
+        return f
+
+    def rhs(self, x, t=0.0):
+        """du/dt for the assembled rows: M^-1 (K x + f(t))."""
+        y = self.asm.Kmat @ x
+        if self.src:
+            y = y + self.source_vector(t)
+        return self.asm.apply_minv(y)
+
+    def lsrk4(self, x, t0, dt, steps, callback=None):
+        res = np.zeros_like(x)
+        t = t0
+        for n in range(steps):
+            for k in range(5):
+                res = LSRK4_A[k] * res + dt * self.rhs(x, t + LSRK4_C[k] * dt)
+                x = x + LSRK4_B[k] * res
+            t += dt
+            if callback is not None:
+                callback(n + 1, t, x)
+        return x
+
+    def leapfrog(self, x, t0, dt, steps, callback=None):
+        """Staggered leapfrog; on return E is at t0 + steps dt, H half a step later."""
+        a = self.asm
+        nE = a.K * a.n3
+        assert a.nblk == 2 and a.flux == "central"
+        x = x.copy()
+        x[nE:] += 0.5 * dt * self.rhs(x, t0)[nE:]
+        t = t0
+        for n in range(steps):
+            x[:nE] += dt * self.rhs(x, t + 0.5 * dt)[:nE]
+            x[nE:] += dt * self.rhs(x, t + dt)[nE:]
+            t += dt
+            if callback is not None:
+                callback(n + 1, t, x)
+        return x
+
+    # -- projection and sampling --------------------------------------------------
+    def project(self, fn, field):
+        """L2 projection of a vector function fn(r [n,3]) -> [n,3] onto field 'E' or 'H'.
+
+        Returns coefficients (K, 3, N) solving M1 c = (fn, phi)_T per element.
+        """
+        a, m = self.asm, self.asm.mesh
+        rq, wq = tet_quadrature(a.p + 4)
+        out = np.empty((a.K, 3, a.N))
+        for T in range(a.K):
+            r = rq @ m.A[T].T + m.b[T][None, :]
+            w = wq * abs(m.det[T])
+            B = a._basis_vectors(T, r)
+            rhs = np.einsum("q,qc,qci->i", w, fn(r), B)
+            out[T] = np.linalg.solve(np.einsum("q,qci,qcj->ij", w, B, B), rhs).reshape(3, a.N)
+        return out
+
+    def evaluate(self, coef, T, r):
+        """Field of element T with coefficients coef (3N,) at points r [n,3] -> [n,3]."""
+        B = self.asm._basis_vectors(T, r)
+        return np.einsum("qci,i->qc", B, coef)
+
+    def l2_error(self, coef, fn, q=None):
+        """L2 norm over the mesh of (field with coefficients coef (K,3,N)) - fn."""
+        a, m = self.asm, self.asm.mesh
+        rq, wq = tet_quadrature(q or a.p + 4)
+        err = 0.0
+        for T in range(a.K):
+            r = rq @ m.A[T].T + m.b[T][None, :]
+            w = wq * abs(m.det[T])
+            v = self.evaluate(coef[T].reshape(-1), T, r) - fn(r)
+            err += float(np.einsum("q,qc,qc->", w, v, v))
+        return math.sqrt(err)
