@@ -1,0 +1,324 @@
+"""Throughput bench of the DG time-domain Maxwell hot path on one GB300.
+
+Workload (one "step" = one LSRK4 time step = five fused right-hand-side /
+stage launches over the whole mesh): the jittered-sphere problem -- 32^3
+Kuhn grid of [0,1]^3 with interior vertices jittered by +-0.15 h (196,608
+tetrahedra), p = 3 (20 modes per component), eps = 4 inside the centred
+sphere of radius 0.25, upwind flux, low-storage RK4, Gaussian pulse
+E_y = exp(-|r - r0|^2 / 0.01).  Synthetic, seeded.
+
+metric: DoF-updates/s = 6 N K S steps / time.  The FP32 path is the headline
+value; the plain FP64 path is measured on the same mesh and reported beside
+it.  Inputs (three field-size buffers) exceed the 129 MB L2.
+
+--impl reference runs the FP64 CPU oracle as it stands (assembled matrices,
+scipy sparse products) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import os
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import argparse
+import json
+import math
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "DoF-updates/s"
+UNIT = "DoF-updates/s"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_problem(w):
+    xyz, tets = w.mesh()
+    c, r, ein, eout = w.extra["sphere"]
+    eps = W.sphere_material(xyz, tets, c, r, ein, eout)
+    return xyz, tets, eps
+
+
+def pulse(r0):
+    r0 = np.asarray(r0)
+
+    def f(r):
+        out = np.zeros((len(r), 6))
+        out[:, 1] = np.exp(-((r - r0[None, :]) ** 2).sum(axis=1) / 0.01)
+        return out
+    return f
+
+
+def stage_bytes(K, N, S, real_size):
+    """Algorithmic DRAM bytes of one LSRK4 step (five stage launches).
+
+    Per stage: read u, write u_out, write res (and read res except in the first
+    stage, whose coefficient a_1 = 0), plus per element the FP64 geometry
+    record (16 doubles) and the neighbour table (4 int32)."""
+    field = 6 * N * K * S * real_size
+    geo = K * (16 * 8 + 4 * 4)
+    return (3 * field + geo) + 4 * (4 * field + geo)
+
+
+def run_gpu(args, precision, steps, warmup, world, rank):
+    import torch
+    from paper_2002_08733_gb300 import dgmax as D
+
+    w = W.jittered_sphere()
+    xyz, tets, eps = build_problem(w)
+    dev = torch.device("cuda", rank % max(torch.cuda.device_count(), 1))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    g = D.Solver(xyz, tets, eps, 1.0, w.p, precision, w.flux, w.integrator, w.dt, device=dev,
+                 stream=stream)
+    g.project(pulse(w.extra["r0"]))
+    K, N, S = g.K, g.N, g.S
+    dofs = 6 * N * K * S
+    t = 0.0
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.advance(1, t)
+            t += w.dt
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(dev.index or 0)
+        with sampler:
+            ev0.record(stream)
+            for _ in range(steps):
+                g.advance(1, t)
+                t += w.dt
+            ev1.record(stream)
+            ev1.synchronize()
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        g.status()
+        energy = float(g.energy()[0])
+    out = dict(precision=precision, ms=ms, steps=steps, dofs=dofs, K=K, N=N, S=S,
+               value=dofs * steps * world / (ms * 1e-3), clocks=sampler.summary(),
+               energy=energy, launches=5 * steps, real_size=g.info.real_size,
+               bytes_fields=g.info.bytes_fields, solver=g, t=t)
+    return out
+
+
+def run_e2e(g, steps, t0):
+    """End-to-end: per step, pinned host state -> device, one step, device -> host."""
+    import torch
+    nbytes = g.info.bytes_fields
+    hin = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    hin.copy_(g.fields[g.current()].view(torch.uint8).reshape(-1).cpu())
+    g.advance_host(hin, hout, 1, t0)     # warm
+    torch.cuda.synchronize()
+    t = t0
+    start = time.perf_counter()
+    for _ in range(steps):
+        g.advance_host(hin, hout, 1, t)
+        t += g.dt
+    el = time.perf_counter() - start
+    dofs = 6 * g.N * g.K * g.S
+    return dict(value=dofs * steps / el, unit=UNIT, h2d_bytes_per_step=int(nbytes),
+                d2h_bytes_per_step=int(nbytes))
+
+
+def cpu_reference(seconds_budget=20.0, n=4):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the same
+    jittered-sphere problem (p, flux, LSRK4, materials, jitter) on an n^3 grid."""
+    from oracle.assemble import Assembly
+    from oracle.mesh import Mesh
+    from oracle.solver import Solver as OSolver
+    w = W.jittered_sphere(n=n)
+    xyz, tets, eps = build_problem(w)
+    o = OSolver(Assembly(Mesh(xyz, tets), w.p, eps, 1.0, w.flux))
+    x = np.zeros((o.asm.ndof, 1))
+    x[:] = 1e-3
+    steps, start = 0, time.perf_counter()
+    while True:
+        x = o.lsrk4(x, 0.0, w.dt, 1)
+        steps += 1
+        el = time.perf_counter() - start
+        if el > seconds_budget or steps >= 1000:
+            break
+    dofs = 6 * o.asm.N * o.asm.K
+    return dict(value=dofs * steps / el, unit=UNIT, cores=1, kind="oracle",
+                sample="jittered-sphere workload on a %d^3 Kuhn grid (%d elements, p=%d), "
+                       "%d LSRK4 steps, assembly excluded" % (n, o.asm.K, w.p, steps)), \
+        (o, w, dofs)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    w = W.jittered_sphere()
+    config = {"workload": "jittered_sphere: 32^3 Kuhn grid of [0,1]^3 (+-0.15h jitter), "
+                          "196608 tets, p=3, eps=4 sphere r=0.25, upwind, LSRK4, "
+                          "Gaussian pulse", "K": w.K, "p": w.p, "S": 1, "dt": w.dt,
+              "l2": "inputs exceed L2 (3 x field buffers > 129 MB)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps, warm = args.steps, args.warmup
+        from oracle.assemble import Assembly
+        from oracle.mesh import Mesh
+        from oracle.solver import Solver as OSolver
+        ws = W.jittered_sphere(n=4)
+        xyz, tets, eps = build_problem(ws)
+        o = OSolver(Assembly(Mesh(xyz, tets), ws.p, eps, 1.0, ws.flux))
+        x = np.full((o.asm.ndof, 1), 1e-3)
+        for _ in range(warm):
+            x = o.lsrk4(x, 0.0, ws.dt, 1)
+        start = time.perf_counter()
+        for _ in range(steps):
+            x = o.lsrk4(x, 0.0, ws.dt, 1)
+        el = time.perf_counter() - start
+        dofs = 6 * o.asm.N * o.asm.K
+        v = dofs * steps / el
+        sample = ("each step: one LSRK4 step of the oracle on the jittered-sphere workload "
+                  "at 4^3 (384 elements, p=3), assembly excluded")
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+                "steps": steps, "warmup": warm, "ms_per_step": el * 1e3 / steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    r32 = run_gpu(args, "fp32", args.steps, args.warmup, world, rank)
+    r64 = run_gpu(args, "fp64", min(args.fp64_steps, args.steps), min(args.warmup, 3), world, rank)
+    e2e = run_e2e(r32["solver"], max(3, min(20, args.steps // 5)), r32["t"])
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    launch_ms = r32["ms"] / r32["launches"]
+    bytes_step = stage_bytes(r32["K"], r32["N"], r32["S"], r32["real_size"])
+    achieved = bytes_step / 5 / (launch_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("fp32_p3_bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "peak_source": peak_src,
+                     "kernel": "stage_kernel<3,float,32,192,LSRK>",
+                     "algorithmic_bytes_per_launch": bytes_step / 5},
+        "fp64": {"value": r64["value"], "ms_per_step": r64["ms"] / r64["steps"],
+                 "steps": r64["steps"], "dtype": "f64"},
+        "fp32_over_fp64": r32["value"] / r64["value"],
+        "e2e": e2e,
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, _ = cpu_reference(seconds_budget=15.0)
+        line["cpu_baseline"] = base
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

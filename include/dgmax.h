@@ -1,0 +1,188 @@
+/*
+ * dgmax.h -- C ABI of the GB300 matrix-free discontinuous Galerkin
+ * time-domain Maxwell solver (Kapidani & Schoeberl, arXiv 2002.08733).
+ *
+ * Problem statement (Sec. I, Eqs. (ampere_cont)/(faraday_cont)): on a
+ * tetrahedral mesh of a domain with per-element permittivity eps and
+ * permeability mu, advance the electric and magnetic fields from initial
+ * values, with PEC walls on the boundary (Sec. IV) and an optional Cartesian
+ * PML (Sec. IV, complex stretching) around a box, driven by point dipoles.
+ *
+ * Discretisation (Secs. II-III): per element, every field component is
+ * expanded in the orthonormal modal basis of degree p on the reference
+ * tetrahedron (Eq. (dubiner_functions), standard collapsed exponents; modes
+ * graded by total degree, then i, then j), mapped covariantly
+ * (Eq. (mapped_eh)).  The state of one column is, per element, 3 covariant
+ * coefficient vectors of E and 3 of H with N = (p+1)(p+2)(p+3)/6 modes each.
+ * The element map uses the element's vertices in ascending global id order.
+ *
+ * Memory layout of a field buffer ("fields"): real numbers (double for
+ * DGM_FP64, float for DGM_FP32), index ((c * N + l) * K + e) * S + s for
+ * component c in 0..5 (Ex, Ey, Ez, Hx, Hy, Hz), mode l, element e, column s.
+ * Auxiliary PML buffers ("aux") use the same layout with K replaced by the
+ * number of PML elements (dgm_info.n_pml) in ascending element order;
+ * components 0..2 hold p, 3..5 hold q (Eqs. (p_variable), (q_variable)).
+ *
+ * Ownership: host inputs are copied by dgm_plan_create.  All device memory
+ * belongs to the caller and is passed by pointer to dgm_bind; the library
+ * allocates no device memory.  Calls are asynchronous on the bound stream
+ * unless stated otherwise.
+ *
+ * Errors: every call returns DGM_OK or one of the codes below; the message
+ * of the last error of the calling thread is returned by dgm_last_error().
+ * Device-side errors are latched in a status word inside the geometry buffer
+ * and reported by the next synchronising call (dgm_energy, dgm_status_check).
+ */
+#ifndef DGMAX_H
+#define DGMAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGM_OK 0
+#define DGM_EINVAL 1   /* invalid argument */
+#define DGM_EMESH 2    /* degenerate element, non-manifold face, bad vertex id */
+#define DGM_EUNSUP 3   /* unsupported order / precision / combination */
+#define DGM_ECUDA 4    /* CUDA runtime error */
+#define DGM_ETIMEOUT 5 /* a device-side wait gave up */
+#define DGM_ENAN 6     /* non-finite values detected */
+#define DGM_ESTATE 7   /* call out of order (e.g. not bound) */
+
+#define DGM_FP64 0
+#define DGM_FP32 1
+
+#define DGM_CENTRAL 0  /* central flux, Eqs. (uwc)/(cwc) */
+#define DGM_UPWIND 1   /* upwind (Riemann) flux */
+
+#define DGM_LEAPFROG 0 /* staggered leapfrog, Sec. V (central flux only) */
+#define DGM_LSRK4 1    /* five-stage low-storage RK4 (Carpenter & Kennedy) */
+
+typedef struct dgm_plan dgm_plan;
+
+typedef struct {
+    int32_t p;          /* polynomial degree of E and H, 1..4 (FP64) or 1..5 (FP32) */
+    int32_t precision;  /* DGM_FP64 or DGM_FP32 field arithmetic; geometry is FP64 */
+    int32_t flux;       /* DGM_CENTRAL or DGM_UPWIND */
+    int32_t integrator; /* DGM_LEAPFROG or DGM_LSRK4 */
+    int32_t n_columns;  /* S >= 1 independent problems (sources) sharing the mesh */
+    int32_t reserved;
+    double dt;          /* time step */
+} dgm_options;
+
+/* Cartesian PML (Sec. IV): the layer is everything outside the box [lo, hi].
+ * Per element the damping triple is sigma_a = sigma_max (d_a / thickness)^order
+ * at the element centroid, d_a its depth into the layer along axis a; the
+ * element then carries eta, xi tensors and auxiliary fields p, q. */
+typedef struct {
+    double lo[3];
+    double hi[3];
+    double thickness;
+    double sigma_max;
+    int32_t order;
+    int32_t reserved;
+} dgm_pml;
+
+typedef struct {
+    int64_t K;            /* elements */
+    int64_t n_pml;        /* elements carrying auxiliary fields */
+    int32_t N;            /* modes per component */
+    int32_t NF;           /* modes per face component */
+    int32_t S;            /* columns */
+    int32_t real_size;    /* bytes per real of the field buffers (4 or 8) */
+    size_t bytes_fields;  /* one field buffer: 6 N K S reals */
+    size_t bytes_aux;     /* one auxiliary buffer: 6 N n_pml S reals (0 without PML) */
+    size_t bytes_geom;    /* geometry + workspace buffer, 256-byte aligned start */
+    int32_t n_quad;       /* projection quadrature points per element */
+    int32_t reserved;
+} dgm_info;
+
+/* Create a plan: validates the mesh, sorts each element's vertices, builds the
+ * face-neighbour table, geometric factors (A^-T, det A), PML tensors and the
+ * reference curl/trace matrices (Sec. III, Eq. (matrix_free_curl)).
+ * xyz: [nv][3] vertex coordinates; tets: [nt][4] vertex ids (any order);
+ * eps, mu: [nt] positive per-element material values; pml may be NULL.
+ * Errors: DGM_EINVAL, DGM_EMESH, DGM_EUNSUP.  No CUDA call is made. */
+int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt,
+                    const int64_t* tets, const double* eps, const double* mu,
+                    const dgm_pml* pml, const dgm_options* opt);
+
+/* Sizes and counts of a plan.  No CUDA call. */
+int dgm_plan_info(const dgm_plan* plan, dgm_info* out);
+
+/* Bind caller-owned device buffers and a CUDA stream (cudaStream_t, may be 0)
+ * and upload the geometry asynchronously.  geom: bytes_geom bytes, 256-byte
+ * aligned; fields0/fields1/res: bytes_fields each (fields1 and res may be NULL
+ * for leapfrog); aux0/aux1/aux_res: bytes_aux each (NULL without PML).
+ * The state lives in fields0 at bind time; see dgm_current. */
+int dgm_bind(dgm_plan* plan, void* geom, void* fields0, void* fields1, void* res,
+             void* aux0, void* aux1, void* aux_res, void* stream);
+
+/* Point dipoles, one per listed column: j = dir delta(r - pos) g(t),
+ * g(t) = sin(2 pi f0 (t - t0)) exp(-(t - t0)^2 / (2 s^2)), s = 1/(2 pi bw).
+ * Enters the E equation as -(j, phi)_T in the element containing pos.
+ * Arrays have n entries (pos, dir: 3 each).  Requires a bound plan; uploads
+ * asynchronously.  Errors: DGM_EINVAL (point outside the mesh, bad column). */
+int dgm_set_sources(dgm_plan* plan, int32_t n, const int32_t* column, const double* pos,
+                    const double* dir, const double* f0, const double* bw, const double* t0);
+
+/* One evaluation of the semi-discrete right-hand side at time t (the hot
+ * path of one stage: reference-curl volume term, face traces, numerical flux,
+ * lift, 3x3 mass-block inverse, PML terms, sources):
+ * dfields = d(fields)/dt, daux = d(aux)/dt (aux/daux NULL without PML).
+ * All pointers are device buffers in the layout above. */
+int dgm_rhs(dgm_plan* plan, const void* fields, const void* aux, void* dfields, void* daux,
+            double t);
+
+/* Leapfrog only: the half step H <- H + dt/2 L_H(E) that starts the staggered
+ * scheme from H given at time t0 (Sec. V). */
+int dgm_leapfrog_start(dgm_plan* plan, double t0);
+
+/* Advance the bound state n_steps time steps from time t0 (asynchronous).
+ * LSRK4 ping-pongs between fields0 and fields1 (and aux0/aux1). */
+int dgm_advance(dgm_plan* plan, int64_t n_steps, double t0);
+
+/* Index (0 or 1) of the bound field/aux buffer that holds the current state. */
+int dgm_current(const dgm_plan* plan);
+
+/* Same as dgm_advance but end to end from host memory: copies fields_in
+ * (host, bytes_fields) to the current device buffer, advances, copies the
+ * result back to fields_out (host) and synchronises the stream. */
+int dgm_advance_host(dgm_plan* plan, const void* fields_in, void* fields_out,
+                     int64_t n_steps, double t0);
+
+/* Discrete energy 1/2 (e . M_eps e + h . M_mu h) per column, accumulated in
+ * FP64 (Sec. III, energy conservation of the central flux).  out: host [S].
+ * Synchronises the stream. */
+int dgm_energy(dgm_plan* plan, const void* fields, double* out);
+
+/* Element ids of the PML elements in auxiliary-buffer order (ascending):
+ * host out[n_pml].  No CUDA call. */
+int dgm_pml_elements(const dgm_plan* plan, int64_t* out);
+
+/* Physical quadrature points used by dgm_project: host [K][n_quad][3]. */
+int dgm_quad_points(const dgm_plan* plan, double* xyz_out);
+
+/* L2 projection of initial values onto the covariant basis (Sec. II).
+ * samples: host [K][n_quad][6] values of (Ex, Ey, Ez, Hx, Hy, Hz) at the
+ * points of dgm_quad_points; writes column `column` of the device buffer
+ * `fields` (synchronous copy on the bound stream). */
+int dgm_project(dgm_plan* plan, const double* samples, int32_t column, void* fields);
+
+/* Read and clear the device status word (synchronises).  Returns DGM_OK or
+ * the latched device error. */
+int dgm_status_check(dgm_plan* plan);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* dgm_last_error(void);
+
+void dgm_plan_destroy(dgm_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGMAX_H */

@@ -1,0 +1,529 @@
+// C ABI of the dgmax library: plans, binding of caller-owned device memory,
+// the time-stepping drivers (LSRK4 stages, leapfrog half steps), the FP64
+// energy reduction, point sources and L2 projection of initial values.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dgm_internal.h"
+#include "dgmax.h"
+
+namespace dgm {
+
+#define DECL(p, r) extern const KernelTable kernels_p##p##_##r;
+DECL(1, f32) DECL(2, f32) DECL(3, f32) DECL(4, f32) DECL(5, f32)
+DECL(1, f64) DECL(2, f64) DECL(3, f64) DECL(4, f64)
+#undef DECL
+
+const KernelTable* kernel_table(int p, int precision) {
+    static const KernelTable* f32[] = {nullptr, &kernels_p1_f32, &kernels_p2_f32, &kernels_p3_f32,
+                                       &kernels_p4_f32, &kernels_p5_f32};
+    static const KernelTable* f64[] = {nullptr, &kernels_p1_f64, &kernels_p2_f64, &kernels_p3_f64,
+                                       &kernels_p4_f64, nullptr};
+    if (p < 1 || p > PMAX) return nullptr;
+    return precision == DGM_FP64 ? f64[p] : (precision == DGM_FP32 ? f32[p] : nullptr);
+}
+
+// Carpenter & Kennedy (1994) five-stage, fourth-order, 2N-storage Runge-Kutta.
+static const double LSRK_A[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                                 -2404267990393.0 / 2016746695238.0,
+                                 -3550918686646.0 / 2091501179385.0,
+                                 -1275806237668.0 / 842570457699.0};
+static const double LSRK_B[5] = {1432997174477.0 / 9575080441755.0,
+                                 5161836677717.0 / 13612068292357.0,
+                                 1720146321549.0 / 2090206949498.0,
+                                 3134564353537.0 / 4481467310338.0,
+                                 2277821191437.0 / 14882151754819.0};
+static const double LSRK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
+                                 2526269341429.0 / 6820363962896.0,
+                                 2006345519317.0 / 3224310063776.0,
+                                 2802321613138.0 / 2924317926251.0};
+
+constexpr int ENERGY_BLOCKS = 304;   // 2 per SM
+constexpr int ENERGY_THREADS = 256;
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace dgm
+
+using namespace dgm;
+
+struct dgm_plan {
+    dgm_options opt;
+    HostMesh mesh;
+    const KernelTable* kt = nullptr;
+    std::vector<double> S, R;   // reference matrices (FP64)
+    int N = 0, NF = 0;
+    bool has_pml = false;
+    // geometry buffer layout (byte offsets)
+    size_t off_geo = 0, off_nbr = 0, off_pml = 0, off_src = 0, off_part = 0, off_status = 0,
+           bytes_geom = 0;
+    std::vector<double> src_host;   // S * (SRC_HDR + 3N)
+    bool have_src = false;
+    // bound state
+    bool bound = false;
+    unsigned char* geom = nullptr;
+    void* fields[2] = {nullptr, nullptr};
+    void* res = nullptr;
+    void* aux[2] = {nullptr, nullptr};
+    void* aux_res = nullptr;
+    cudaStream_t stream = nullptr;
+    int cur = 0;
+    int device = -1;
+};
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+    return fail(DGM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// FP64 energy: W_s = 1/2 sum_T |det| sum_l (eps u_l^T G u_l + mu h_l^T G h_l), G = A^-1 A^-T
+template <typename R>
+__global__ void __launch_bounds__(ENERGY_THREADS)
+energy_partial(const R* __restrict__ u, const double* __restrict__ geo, int64_t K, int S, int N,
+               double* __restrict__ part) {
+    __shared__ double red[ENERGY_THREADS];
+    const int s = blockIdx.y;
+    const int64_t C = K * S;
+    double acc = 0.0;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < K;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        double a[9];
+        for (int k = 0; k < 9; ++k) a[k] = geo[int64_t(G_AIT + k) * K + e];
+        double G[3][3];   // G = Ait^T Ait
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) G[i][j] = a[i] * a[j] + a[3 + i] * a[3 + j] + a[6 + i] * a[6 + j];
+        const double vol = fabs(geo[int64_t(G_DET) * K + e]);
+        const double mat[2] = {geo[int64_t(G_EPS) * K + e], geo[int64_t(G_MU) * K + e]};
+        const int64_t col = e * S + s;
+        double w = 0.0;
+        for (int fld = 0; fld < 2; ++fld) {
+            double wf = 0.0;
+            for (int l = 0; l < N; ++l) {
+                double v[3];
+                for (int j = 0; j < 3; ++j) v[j] = double(u[int64_t((3 * fld + j) * N + l) * C + col]);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) wf += v[i] * G[i][j] * v[j];
+            }
+            w += mat[fld] * wf;
+        }
+        acc += 0.5 * vol * w;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = ENERGY_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[int64_t(s) * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void energy_final(const double* __restrict__ part, int nblk, int S, double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double acc = 0.0;
+    for (int b = 0; b < nblk; ++b) acc += part[int64_t(s) * nblk + b];
+    out[s] = acc;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* dgm_last_error(void) { return g_err.c_str(); }
+
+int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, const int64_t* tets,
+                    const double* eps, const double* mu, const dgm_pml* pml,
+                    const dgm_options* opt) {
+    if (!out || !opt) return fail(DGM_EINVAL, "null plan pointer or options");
+    *out = nullptr;
+    if (opt->n_columns < 1) return fail(DGM_EINVAL, "n_columns must be >= 1");
+    if (!(opt->dt > 0.0) || !std::isfinite(opt->dt)) return fail(DGM_EINVAL, "dt must be positive");
+    if (opt->flux != DGM_CENTRAL && opt->flux != DGM_UPWIND) return fail(DGM_EINVAL, "unknown flux");
+    if (opt->integrator != DGM_LEAPFROG && opt->integrator != DGM_LSRK4)
+        return fail(DGM_EINVAL, "unknown integrator");
+    if (opt->integrator == DGM_LEAPFROG && (opt->flux != DGM_CENTRAL || pml))
+        return fail(DGM_EUNSUP, "leapfrog needs the central flux and no PML");
+    const KernelTable* kt = kernel_table(opt->p, opt->precision);
+    if (!kt) return fail(DGM_EUNSUP, "unsupported polynomial degree / precision");
+    if (pml) {
+        if (!(pml->thickness > 0.0) || !(pml->sigma_max >= 0.0) || pml->order < 0)
+            return fail(DGM_EINVAL, "invalid PML parameters");
+        for (int a = 0; a < 3; ++a)
+            if (!(pml->hi[a] > pml->lo[a])) return fail(DGM_EINVAL, "invalid PML box");
+    }
+    dgm_plan* P = new dgm_plan();
+    P->opt = *opt;
+    P->kt = kt;
+    P->N = nmodes(opt->p);
+    P->NF = nfmodes(opt->p);
+    P->has_pml = pml != nullptr;
+    std::string err;
+    int rc = build_mesh(nv, xyz, nt, tets, eps, mu, pml ? pml->lo : nullptr, pml ? pml->hi : nullptr,
+                        pml ? pml->thickness : 1.0, pml ? pml->sigma_max : 0.0,
+                        pml ? pml->order : 0, P->has_pml, P->mesh, err);
+    if (rc) {
+        delete P;
+        return fail(rc, err);
+    }
+    if (build_refmats(opt->p, P->S, P->R, err)) {
+        delete P;
+        return fail(DGM_EINVAL, err);
+    }
+    const int64_t K = P->mesh.K;
+    const int Sc = opt->n_columns;
+    size_t off = 0;
+    P->off_geo = off;
+    off = align256(off + sizeof(double) * G_COUNT * K);
+    P->off_nbr = off;
+    off = align256(off + sizeof(int32_t) * 4 * K);
+    P->off_pml = off;
+    off = align256(off + sizeof(int32_t) * K);
+    P->off_src = off;
+    off = align256(off + sizeof(double) * size_t(Sc) * (SRC_HDR + 3 * P->N));
+    P->off_part = off;
+    off = align256(off + sizeof(double) * (size_t(Sc) * ENERGY_BLOCKS + Sc));
+    P->off_status = off;
+    off = align256(off + 64);
+    P->bytes_geom = off;
+    P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
+    for (int s = 0; s < Sc; ++s) P->src_host[size_t(s) * (SRC_HDR + 3 * P->N)] = -1.0;
+    *out = P;
+    return DGM_OK;
+}
+
+void dgm_plan_destroy(dgm_plan* plan) { delete plan; }
+
+int dgm_plan_info(const dgm_plan* P, dgm_info* out) {
+    if (!P || !out) return fail(DGM_EINVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->K = P->mesh.K;
+    out->n_pml = P->mesh.npml;
+    out->N = P->N;
+    out->NF = P->NF;
+    out->S = P->opt.n_columns;
+    out->real_size = P->kt->real_size;
+    out->bytes_fields = size_t(6) * P->N * P->mesh.K * P->opt.n_columns * P->kt->real_size;
+    out->bytes_aux = size_t(6) * P->N * P->mesh.npml * P->opt.n_columns * P->kt->real_size;
+    out->bytes_geom = P->bytes_geom;
+    out->n_quad = (P->opt.p + 3) * (P->opt.p + 3) * (P->opt.p + 3);
+    return DGM_OK;
+}
+
+int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, void* aux0,
+             void* aux1, void* aux_res, void* stream) {
+    if (!P || !geom || !fields0) return fail(DGM_EINVAL, "null plan, geometry or field buffer");
+    if (reinterpret_cast<uintptr_t>(geom) % 256) return fail(DGM_EINVAL, "geometry buffer must be 256-byte aligned");
+    if (P->opt.integrator == DGM_LSRK4 && (!fields1 || !res))
+        return fail(DGM_EINVAL, "LSRK4 needs fields1 and res");
+    if (P->has_pml && P->mesh.npml > 0 && (!aux0 || (P->opt.integrator == DGM_LSRK4 && (!aux1 || !aux_res))))
+        return fail(DGM_EINVAL, "PML plan needs auxiliary buffers");
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    P->geom = static_cast<unsigned char*>(geom);
+    P->fields[0] = fields0;
+    P->fields[1] = fields1;
+    P->res = res;
+    P->aux[0] = aux0;
+    P->aux[1] = aux1;
+    P->aux_res = aux_res;
+    P->stream = static_cast<cudaStream_t>(stream);
+    P->cur = 0;
+    const int64_t K = P->mesh.K;
+    cudaStream_t st = P->stream;
+    if ((e = cudaMemcpyAsync(P->geom + P->off_geo, P->mesh.geo.data(), sizeof(double) * G_COUNT * K,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "upload geometry");
+    if ((e = cudaMemcpyAsync(P->geom + P->off_nbr, P->mesh.nbr.data(), sizeof(int32_t) * 4 * K,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "upload neighbours");
+    if ((e = cudaMemcpyAsync(P->geom + P->off_pml, P->mesh.pml_idx.data(), sizeof(int32_t) * K,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "upload PML index");
+    if ((e = cudaMemcpyAsync(P->geom + P->off_src, P->src_host.data(),
+                             sizeof(double) * P->src_host.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_fail(e, "upload sources");
+    if ((e = cudaMemsetAsync(P->geom + P->off_status, 0, 64, st)) != cudaSuccess)
+        return cuda_fail(e, "clear status");
+    // the host copies above are pageable: finish them before the host vectors can change
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
+    int rc = P->kt->set_refmats(P->S.data(), P->R.data());
+    if (rc) return fail(rc, "upload reference matrices");
+    P->bound = true;
+    return DGM_OK;
+}
+
+static void stage_params(dgm_plan* P, StageParams& prm) {
+    std::memset(&prm, 0, sizeof(prm));
+    prm.geo = reinterpret_cast<const double*>(P->geom + P->off_geo);
+    prm.nbr = reinterpret_cast<const int32_t*>(P->geom + P->off_nbr);
+    prm.pml = P->has_pml ? reinterpret_cast<const int32_t*>(P->geom + P->off_pml) : nullptr;
+    prm.src = P->have_src ? reinterpret_cast<const double*>(P->geom + P->off_src) : nullptr;
+    prm.status = reinterpret_cast<int32_t*>(P->geom + P->off_status);
+    prm.K = P->mesh.K;
+    prm.npml = P->mesh.npml;
+    prm.S = P->opt.n_columns;
+    prm.upwind = P->opt.flux == DGM_UPWIND;
+    prm.dt = P->opt.dt;
+}
+
+int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double* pos,
+                    const double* dir, const double* f0, const double* bw, const double* t0) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (n < 0 || (n > 0 && (!column || !pos || !dir || !f0 || !bw || !t0)))
+        return fail(DGM_EINVAL, "invalid source arrays");
+    const int N = P->N;
+    const size_t rec = SRC_HDR + 3 * N;
+    const int64_t K = P->mesh.K;
+    std::vector<double> host(P->src_host.size(), 0.0);
+    for (int s = 0; s < P->opt.n_columns; ++s) host[s * rec] = -1.0;
+    for (int i = 0; i < n; ++i) {
+        const int s = column[i];
+        if (s < 0 || s >= P->opt.n_columns) return fail(DGM_EINVAL, "source column out of range");
+        if (host[s * rec] >= 0.0) return fail(DGM_EINVAL, "one source per column");
+        if (!(bw[i] > 0.0)) return fail(DGM_EINVAL, "source bandwidth must be positive");
+        const double* r = pos + 3 * i;
+        int64_t found = -1;
+        double xr[3];
+        for (int64_t e = 0; e < K && found < 0; ++e) {
+            const double* V = &P->mesh.verts[12 * e];
+            double d[3] = {r[0] - V[0], r[1] - V[1], r[2] - V[2]};
+            double lam[3];
+            for (int a = 0; a < 3; ++a)   // r_hat = A^-1 (r - v0), A^-1[a][c] = Ait[c][a]
+                lam[a] = P->mesh.geo[(G_AIT + 3 * 0 + a) * K + e] * d[0] +
+                         P->mesh.geo[(G_AIT + 3 * 1 + a) * K + e] * d[1] +
+                         P->mesh.geo[(G_AIT + 3 * 2 + a) * K + e] * d[2];
+            const double tol = 1e-12;
+            if (lam[0] >= -tol && lam[1] >= -tol && lam[2] >= -tol && lam[0] + lam[1] + lam[2] <= 1 + tol) {
+                found = e;
+                for (int a = 0; a < 3; ++a) xr[a] = lam[a];
+            }
+        }
+        if (found < 0) return fail(DGM_EINVAL, "source point outside the mesh");
+        double* out = &host[s * rec];
+        out[0] = double(found);
+        out[1] = f0[i];
+        out[2] = bw[i];
+        out[3] = t0[i];
+        std::vector<double> phi(N);
+        ref_basis_values(P->opt.p, xr, phi.data());
+        // w_{j,l} = dir . (A^-T e_j) phi_l(r_hat) = sum_c Ait[c][j] dir_c phi_l
+        for (int j = 0; j < 3; ++j) {
+            double dj = 0.0;
+            for (int cc = 0; cc < 3; ++cc) dj += P->mesh.geo[(G_AIT + 3 * cc + j) * K + found] * dir[3 * i + cc];
+            for (int l = 0; l < N; ++l) out[SRC_HDR + j * N + l] = dj * phi[l];
+        }
+    }
+    P->src_host = host;
+    P->have_src = n > 0;
+    cudaError_t e = cudaMemcpyAsync(P->geom + P->off_src, P->src_host.data(),
+                                    sizeof(double) * P->src_host.size(), cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload sources");
+    if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "source sync");
+    return DGM_OK;
+}
+
+int dgm_rhs(dgm_plan* P, const void* fields, const void* aux, void* dfields, void* daux, double t) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!fields || !dfields) return fail(DGM_EINVAL, "null field buffer");
+    if (P->has_pml && P->mesh.npml > 0 && (!aux || !daux)) return fail(DGM_EINVAL, "PML plan needs aux/daux");
+    StageParams prm;
+    stage_params(P, prm);
+    prm.u = fields;
+    prm.u_out = dfields;
+    prm.aux = aux;
+    prm.aux_out = daux;
+    prm.t = t;
+    int rc = P->kt->launch_stage(prm, MODE_RHS, P->stream);
+    return rc ? fail(rc, "stage kernel launch failed") : DGM_OK;
+}
+
+int dgm_leapfrog_start(dgm_plan* P, double t0) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (P->opt.integrator != DGM_LEAPFROG) return fail(DGM_ESTATE, "not a leapfrog plan");
+    StageParams prm;
+    stage_params(P, prm);
+    prm.u = P->fields[P->cur];
+    prm.u_out = P->fields[P->cur];
+    prm.dt = 0.5 * P->opt.dt;
+    prm.t = t0;
+    int rc = P->kt->launch_stage(prm, MODE_LF_H, P->stream);
+    return rc ? fail(rc, "stage kernel launch failed") : DGM_OK;
+}
+
+int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (n_steps < 0) return fail(DGM_EINVAL, "negative step count");
+    StageParams prm;
+    stage_params(P, prm);
+    const double dt = P->opt.dt;
+    for (int64_t n = 0; n < n_steps; ++n) {
+        const double t = t0 + double(n) * dt;
+        if (P->opt.integrator == DGM_LSRK4) {
+            for (int k = 0; k < 5; ++k) {
+                prm.u = P->fields[P->cur];
+                prm.u_out = P->fields[1 - P->cur];
+                prm.res = P->res;
+                prm.aux = P->aux[P->cur];
+                prm.aux_out = P->aux[1 - P->cur];
+                prm.aux_res = P->aux_res;
+                prm.t = t + LSRK_C[k] * dt;
+                prm.a = LSRK_A[k];
+                prm.b = LSRK_B[k];
+                int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+                if (rc) return fail(rc, "stage kernel launch failed");
+                P->cur = 1 - P->cur;
+            }
+        } else {
+            prm.u = P->fields[P->cur];
+            prm.u_out = P->fields[P->cur];
+            prm.t = t + 0.5 * dt;
+            int rc = P->kt->launch_stage(prm, MODE_LF_E, P->stream);
+            if (rc) return fail(rc, "stage kernel launch failed");
+            prm.t = t + dt;
+            rc = P->kt->launch_stage(prm, MODE_LF_H, P->stream);
+            if (rc) return fail(rc, "stage kernel launch failed");
+        }
+    }
+    return DGM_OK;
+}
+
+int dgm_current(const dgm_plan* P) { return P ? P->cur : -1; }
+
+int dgm_advance_host(dgm_plan* P, const void* fields_in, void* fields_out, int64_t n_steps, double t0) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!fields_in || !fields_out) return fail(DGM_EINVAL, "null host buffer");
+    dgm_info info;
+    dgm_plan_info(P, &info);
+    cudaError_t e = cudaMemcpyAsync(P->fields[P->cur], fields_in, info.bytes_fields,
+                                    cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+    int rc = dgm_advance(P, n_steps, t0);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(fields_out, P->fields[P->cur], info.bytes_fields, cudaMemcpyDeviceToHost, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+    e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return DGM_OK;
+}
+
+int dgm_energy(dgm_plan* P, const void* fields, double* out) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!fields || !out) return fail(DGM_EINVAL, "null argument");
+    const int Sc = P->opt.n_columns;
+    double* part = reinterpret_cast<double*>(P->geom + P->off_part);
+    double* res = part + size_t(Sc) * ENERGY_BLOCKS;
+    const double* geo = reinterpret_cast<const double*>(P->geom + P->off_geo);
+    dim3 grid(ENERGY_BLOCKS, Sc);
+    if (P->kt->real_size == 8)
+        energy_partial<double><<<grid, ENERGY_THREADS, 0, P->stream>>>(
+            static_cast<const double*>(fields), geo, P->mesh.K, Sc, P->N, part);
+    else
+        energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
+            static_cast<const float*>(fields), geo, P->mesh.K, Sc, P->N, part);
+    energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(part, ENERGY_BLOCKS, Sc, res);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
+    e = cudaMemcpyAsync(out, res, sizeof(double) * Sc, cudaMemcpyDeviceToHost, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "energy copy");
+    e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "energy sync");
+    return DGM_OK;
+}
+
+int dgm_pml_elements(const dgm_plan* P, int64_t* out) {
+    if (!P || (!out && P->mesh.npml > 0)) return fail(DGM_EINVAL, "null argument");
+    for (int64_t e = 0; e < P->mesh.K; ++e)
+        if (P->mesh.pml_idx[e] >= 0) out[P->mesh.pml_idx[e]] = e;
+    return DGM_OK;
+}
+
+int dgm_quad_points(const dgm_plan* P, double* xyz_out) {
+    if (!P || !xyz_out) return fail(DGM_EINVAL, "null argument");
+    std::vector<double> pts, w;
+    tet_rule(P->opt.p + 3, pts, w);
+    const size_t nq = w.size();
+    const int64_t K = P->mesh.K;
+    for (int64_t e = 0; e < K; ++e) {
+        const double* V = &P->mesh.verts[12 * e];
+        for (size_t q = 0; q < nq; ++q)
+            for (int a = 0; a < 3; ++a)
+                xyz_out[(e * nq + q) * 3 + a] = V[a] + pts[3 * q] * (V[3 + a] - V[a]) +
+                                                pts[3 * q + 1] * (V[6 + a] - V[a]) +
+                                                pts[3 * q + 2] * (V[9 + a] - V[a]);
+    }
+    return DGM_OK;
+}
+
+int dgm_project(dgm_plan* P, const double* samples, int32_t column, void* fields) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!samples || !fields || column < 0 || column >= P->opt.n_columns)
+        return fail(DGM_EINVAL, "invalid projection arguments");
+    std::vector<double> pts, w;
+    tet_rule(P->opt.p + 3, pts, w);
+    const size_t nq = w.size();
+    const int64_t K = P->mesh.K;
+    const int N = P->N;
+    std::vector<double> phi(nq * N);
+    for (size_t q = 0; q < nq; ++q) ref_basis_values(P->opt.p, &pts[3 * q], &phi[q * N]);
+    // covariant coefficients u_l = A^T sum_q w_q phi_l(q) f(r_q)  (closed-form block mass inverse)
+    const int rs = P->kt->real_size;
+    std::vector<unsigned char> host(size_t(6) * N * K * rs);
+    for (int64_t e = 0; e < K; ++e) {
+        double AT[3][3];   // A^T[j][r] = edge j, coordinate r
+        const double* V = &P->mesh.verts[12 * e];
+        for (int j = 0; j < 3; ++j)
+            for (int r = 0; r < 3; ++r) AT[j][r] = V[3 * (j + 1) + r] - V[r];
+        for (int fld = 0; fld < 2; ++fld)
+            for (int l = 0; l < N; ++l) {
+                double m[3] = {0, 0, 0};
+                for (size_t q = 0; q < nq; ++q) {
+                    const double* f = &samples[(e * nq + q) * 6 + 3 * fld];
+                    for (int r = 0; r < 3; ++r) m[r] += w[q] * phi[q * N + l] * f[r];
+                }
+                for (int j = 0; j < 3; ++j) {
+                    const double v = AT[j][0] * m[0] + AT[j][1] * m[1] + AT[j][2] * m[2];
+                    const size_t idx = size_t((3 * fld + j) * N + l) * K + e;
+                    if (rs == 8)
+                        reinterpret_cast<double*>(host.data())[idx] = v;
+                    else
+                        reinterpret_cast<float*>(host.data())[idx] = float(v);
+                }
+            }
+    }
+    const int Sc = P->opt.n_columns;
+    cudaError_t e = cudaMemcpy2DAsync(static_cast<unsigned char*>(fields) + size_t(column) * rs,
+                                      size_t(Sc) * rs, host.data(), rs, rs, size_t(6) * N * K,
+                                      cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "projection copy");
+    e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "projection sync");
+    return DGM_OK;
+}
+
+int dgm_status_check(dgm_plan* P) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, P->geom + P->off_status, sizeof(st), cudaMemcpyDeviceToHost, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status copy");
+    if ((e = cudaMemsetAsync(P->geom + P->off_status, 0, sizeof(st), P->stream)) != cudaSuccess)
+        return cuda_fail(e, "status clear");
+    if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "status sync");
+    if (st & ST_TIMEOUT) return fail(DGM_ETIMEOUT, "a device-side wait gave up");
+    if (st & ST_NAN) return fail(DGM_ENAN, "non-finite values detected");
+    if (st & ST_BAD_NEIGHBOUR) return fail(DGM_EMESH, "out-of-range neighbour index on the device");
+    return DGM_OK;
+}
+
+}  // extern "C"

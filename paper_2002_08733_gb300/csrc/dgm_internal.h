@@ -1,0 +1,89 @@
+// Internal declarations shared by the host setup, the C ABI and the kernel
+// translation units of the dgmax library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace dgm {
+
+constexpr int PMAX = 5;
+
+__host__ __device__ constexpr int nmodes(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+__host__ __device__ constexpr int nfmodes(int p) { return (p + 1) * (p + 2) / 2; }
+
+// Per-element FP64 record, stored structure-of-arrays: geo[k * K + e].
+enum GeoSlot {
+    G_AIT = 0,    // 9 entries of A^-T, row major
+    G_DET = 9,    // signed det A
+    G_EPS = 10,
+    G_MU = 11,
+    G_SIG = 12,   // 3 PML damping values
+    G_PAD = 15,
+    G_COUNT = 16
+};
+
+// Source record per column (FP64): [elem, f0, bw, t0, 0,0,0,0, w[3N]].
+constexpr int SRC_HDR = 8;
+
+enum Mode { MODE_RHS = 0, MODE_LSRK = 1, MODE_LF_E = 2, MODE_LF_H = 3 };
+
+enum StatusBits { ST_OK = 0, ST_BAD_NEIGHBOUR = 1, ST_NAN = 2, ST_TIMEOUT = 4 };
+
+struct StageParams {
+    const void* u;        // fields in  [6][N][K][S]
+    void* u_out;          // LSRK: other buffer; leapfrog: same buffer; RHS: du
+    void* res;            // LSRK residual
+    const void* aux;      // PML auxiliaries in [6][N][P][S]
+    void* aux_out;
+    void* aux_res;
+    const double* geo;    // [G_COUNT][K]
+    const int32_t* nbr;   // [4][K]: (neighbour << 2) | neighbour's local face, or -1
+    const int32_t* pml;   // [K]: index into aux, or -1 (may be null without PML)
+    const double* src;    // [S][SRC_HDR + 3N] or null
+    int32_t* status;      // device status word
+    int64_t K;
+    int64_t npml;
+    int32_t S;
+    int32_t upwind;
+    double t, dt, a, b;   // stage time, step, LSRK coefficients a_k, b_k
+};
+
+// Kernel translation unit entry points, one set per (order, precision).
+struct KernelTable {
+    int (*launch_stage)(const StageParams&, int mode, void* stream);
+    int (*set_refmats)(const double* S, const double* R);  // S[3][N][N], R[4][NF][N]
+    int real_size;
+};
+
+const KernelTable* kernel_table(int p, int precision);
+
+// Host setup (dgm_setup.cpp)
+struct HostMesh {
+    int64_t K = 0;
+    std::vector<double> geo;          // G_COUNT * K
+    std::vector<int32_t> nbr;         // 4 * K
+    std::vector<int32_t> pml_idx;     // K
+    std::vector<double> verts;        // K * 12 (sorted local vertices)
+    int64_t npml = 0;
+};
+
+int build_mesh(int64_t nv, const double* xyz, int64_t nt, const int64_t* tets, const double* eps,
+               const double* mu, const double* pml_lo, const double* pml_hi, double pml_L,
+               double pml_smax, int pml_order, bool has_pml, HostMesh& out, std::string& err);
+
+// Reference matrices on the reference tetrahedron (dgm_refmats.cpp):
+// S[a][l][m] = int phi_l d_a phi_m, R[f][m][l] = int_{face f} psi_m phi_l (ds dt).
+int build_refmats(int p, std::vector<double>& S, std::vector<double>& R, std::string& err);
+
+// Reference basis values at reference points (for projection, sources): out[N].
+void ref_basis_values(int p, const double xr[3], double* out);
+
+// Collapsed Gauss-Legendre rule on the reference tetrahedron.
+void tet_rule(int q, std::vector<double>& pts, std::vector<double>& w);
+
+}  // namespace dgm

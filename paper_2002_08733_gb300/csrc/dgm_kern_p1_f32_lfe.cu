@@ -1,0 +1,7 @@
+// Fused stage kernel: degree 1, float fields, leapfrog E half step.
+#define DGM_P 1
+#define DGM_REAL float
+#define DGM_MODE MODE_LF_E
+#define DGM_LAUNCH launch_p1_f32_lfe
+#define DGM_SETREF setref_p1_f32_lfe
+#include "dgm_kern_impl.cuh"

@@ -1,0 +1,279 @@
+"""Python binding of the dgmax C ABI (include/dgmax.h).
+
+Argument marshalling only: every step of the right-hand side and of the time
+stepping runs in the CUDA kernels of libdgmax.so.  PyTorch provides device
+memory and the stream.  There is no CPU fallback: if the library is missing
+or fails to load, the constructor raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libdgmax.so")
+
+FP64, FP32 = 0, 1
+CENTRAL, UPWIND = 0, 1
+LEAPFROG, LSRK4 = 0, 1
+
+STATUS = {0: "DGM_OK", 1: "DGM_EINVAL", 2: "DGM_EMESH", 3: "DGM_EUNSUP", 4: "DGM_ECUDA",
+          5: "DGM_ETIMEOUT", 6: "DGM_ENAN", 7: "DGM_ESTATE"}
+
+
+class DgmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("precision", ctypes.c_int32), ("flux", ctypes.c_int32),
+                ("integrator", ctypes.c_int32), ("n_columns", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("dt", ctypes.c_double)]
+
+
+class Pml(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("thickness", ctypes.c_double), ("sigma_max", ctypes.c_double),
+                ("order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("n_pml", ctypes.c_int64), ("N", ctypes.c_int32),
+                ("NF", ctypes.c_int32), ("S", ctypes.c_int32), ("real_size", ctypes.c_int32),
+                ("bytes_fields", ctypes.c_size_t), ("bytes_aux", ctypes.c_size_t),
+                ("bytes_geom", ctypes.c_size_t), ("n_quad", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "dgm_plan_create": [ctypes.POINTER(_P), ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P,
+                        ctypes.POINTER(Pml), ctypes.POINTER(Options)],
+    "dgm_plan_info": [_P, ctypes.POINTER(Info)],
+    "dgm_bind": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "dgm_set_sources": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
+    "dgm_rhs": [_P, _P, _P, _P, _P, ctypes.c_double],
+    "dgm_leapfrog_start": [_P, ctypes.c_double],
+    "dgm_advance": [_P, ctypes.c_int64, ctypes.c_double],
+    "dgm_current": [_P],
+    "dgm_advance_host": [_P, _P, _P, ctypes.c_int64, ctypes.c_double],
+    "dgm_energy": [_P, _P, _P],
+    "dgm_pml_elements": [_P, _P],
+    "dgm_quad_points": [_P, _P],
+    "dgm_project": [_P, _P, ctypes.c_int32, _P],
+    "dgm_status_check": [_P],
+    "dgm_last_error": [],
+    "dgm_plan_destroy": [_P],
+}
+
+
+def load_library(path=LIB_PATH):
+    """Load libdgmax.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdgmax.so not built (%s); run paper_2002_08733_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.dgm_last_error.restype = ctypes.c_char_p
+    lib.dgm_plan_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise DgmError(rc, _lib.dgm_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Plan:
+    """Host-side plan (mesh setup, reference matrices); no GPU needed."""
+
+    def __init__(self, xyz, tets, eps, mu, p, precision="fp64", flux="upwind",
+                 integrator="lsrk4", dt=1e-3, S=1, pml=None):
+        lib = load_library()
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int64)
+        K = tets.shape[0]
+        self.eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (K,)))
+        self.mu = np.ascontiguousarray(np.broadcast_to(np.asarray(mu, np.float64), (K,)))
+        opt = Options(p=p, precision={"fp64": FP64, "fp32": FP32}[precision],
+                      flux={"central": CENTRAL, "upwind": UPWIND}[flux],
+                      integrator={"leapfrog": LEAPFROG, "lsrk4": LSRK4}[integrator],
+                      n_columns=S, dt=dt)
+        pm = None
+        if pml is not None:
+            pm = Pml()
+            pm.lo[:] = list(pml["lo"])
+            pm.hi[:] = list(pml["hi"])
+            pm.thickness = pml["thickness"]
+            pm.sigma_max = pml["sigma_max"]
+            pm.order = pml.get("order", 2)
+        h = _P()
+        _check(lib.dgm_plan_create(ctypes.byref(h), xyz.shape[0], xyz.ctypes.data, K,
+                                   tets.ctypes.data, self.eps.ctypes.data, self.mu.ctypes.data,
+                                   ctypes.byref(pm) if pm is not None else None, ctypes.byref(opt)))
+        self.handle = h
+        self.opt = opt
+        self.precision = precision
+        info = Info()
+        _check(lib.dgm_plan_info(h, ctypes.byref(info)))
+        self.info = info
+        self.K, self.N, self.S, self.npml = info.K, info.N, info.S, info.n_pml
+        self.p = p
+        self.dt = dt
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dgm_plan_destroy(self.handle)
+            self.handle = None
+
+    def pml_elements(self):
+        """Element ids carrying auxiliary fields, in auxiliary-buffer order."""
+        if not hasattr(self, "_pml_el"):
+            out = np.zeros(max(self.npml, 1), dtype=np.int64)
+            _check(_lib.dgm_pml_elements(self.handle, out.ctypes.data))
+            self._pml_el = out[:self.npml]
+        return self._pml_el
+
+    def quad_points(self):
+        out = np.empty((self.K, self.info.n_quad, 3))
+        _check(_lib.dgm_quad_points(self.handle, out.ctypes.data))
+        return out
+
+
+class Solver(Plan):
+    """Plan bound to caller-owned torch device buffers on one CUDA device."""
+
+    def __init__(self, *args, device="cuda", stream=None, **kw):
+        super().__init__(*args, **kw)
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        dt = torch.float64 if self.precision == "fp64" else torch.float32
+        self.dtype = dt
+        i = self.info
+        shape = (6, self.N, self.K, self.S)
+        self.geom = torch.empty(i.bytes_geom + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.geom.data_ptr()) % 256
+        self.geom_view = self.geom[off:off + i.bytes_geom]
+        self.fields = [torch.zeros(shape, dtype=dt, device=self.device) for _ in range(2)]
+        self.res = torch.zeros(shape, dtype=dt, device=self.device)
+        ashape = (6, self.N, self.npml, self.S)
+        if self.npml > 0:
+            self.aux = [torch.zeros(ashape, dtype=dt, device=self.device) for _ in range(2)]
+            self.aux_res = torch.zeros(ashape, dtype=dt, device=self.device)
+        else:
+            self.aux = [None, None]
+            self.aux_res = None
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        torch.cuda.synchronize(self.device)   # allocations above ran on torch's stream
+        _check(_lib.dgm_bind(self.handle, self.geom_view.data_ptr(), _ptr(self.fields[0]),
+                             _ptr(self.fields[1]), _ptr(self.res), _ptr(self.aux[0]),
+                             _ptr(self.aux[1]), _ptr(self.aux_res), self.stream.cuda_stream))
+
+    # -- layout conversion between (K, S, 6, N) and the device layout [6][N][K][S]
+    def to_device(self, u):
+        t = self.torch.as_tensor(np.ascontiguousarray(np.transpose(np.asarray(u), (2, 3, 0, 1))))
+        return t.to(device=self.device, dtype=self.dtype).contiguous()
+
+    def aux_to_device(self, aux_full):
+        """aux given for all K elements (K, S, 6, N) -> compact PML layout."""
+        idx = self.pml_elements()
+        return self.to_device(np.asarray(aux_full)[idx])
+
+    @staticmethod
+    def from_device(t):
+        return np.transpose(t.double().cpu().numpy(), (2, 3, 0, 1)).copy()
+
+
+    def current(self):
+        return _lib.dgm_current(self.handle)
+
+    def set_state(self, u, aux=None):
+        self.torch.cuda.synchronize(self.device)
+        self.fields[self.current()].copy_(self.to_device(u))
+        if aux is not None and self.npml > 0:
+            self.aux[self.current()].copy_(aux if self.torch.is_tensor(aux) else self.to_device(aux))
+        self.torch.cuda.synchronize(self.device)
+
+    def state(self):
+        self.torch.cuda.synchronize(self.device)
+        return self.from_device(self.fields[self.current()])
+
+    def rhs(self, u, aux=None, t=0.0):
+        """One right-hand-side evaluation; u: (K, S, 6, N) array -> du (same shape)."""
+        ud = u if self.torch.is_tensor(u) else self.to_device(u)
+        du = self.torch.empty_like(ud)
+        ad = dad = None
+        if self.npml > 0:
+            ad = aux if self.torch.is_tensor(aux) else (
+                self.to_device(aux) if aux is not None else self.torch.zeros_like(self.aux[0]))
+            dad = self.torch.empty_like(ad)
+        _check(_lib.dgm_rhs(self.handle, _ptr(ud), _ptr(ad), _ptr(du), _ptr(dad), t))
+        self.torch.cuda.synchronize(self.device)
+        if self.npml > 0:
+            return du, dad
+        return du
+
+    def advance(self, n_steps, t0=0.0):
+        _check(_lib.dgm_advance(self.handle, int(n_steps), float(t0)))
+
+    def leapfrog_start(self, t0=0.0):
+        _check(_lib.dgm_leapfrog_start(self.handle, float(t0)))
+
+    def advance_host(self, host_in, host_out, n_steps, t0=0.0):
+        """End-to-end call from host memory (torch pinned CPU tensors or numpy arrays)."""
+        _check(_lib.dgm_advance_host(self.handle, _ptr(host_in), _ptr(host_out), int(n_steps),
+                                     float(t0)))
+
+    def energy(self, fields=None):
+        f = self.fields[self.current()] if fields is None else fields
+        out = np.zeros(self.S)
+        _check(_lib.dgm_energy(self.handle, _ptr(f), out.ctypes.data))
+        return out
+
+    def project(self, fn, column=0):
+        """L2 projection of fn(points [n,3]) -> [n,6] (E, H) into the current state."""
+        pts = self.quad_points()
+        vals = np.ascontiguousarray(fn(pts.reshape(-1, 3)).reshape(self.K, -1, 6), dtype=np.float64)
+        _check(_lib.dgm_project(self.handle, vals.ctypes.data, column,
+                                _ptr(self.fields[self.current()])))
+
+    def set_sources(self, sources):
+        """sources: list over columns of dict(pos, dir, f0, bw, t0) or None."""
+        cols, pos, dirs, f0, bw, t0 = [], [], [], [], [], []
+        for s, rec in enumerate(sources):
+            if rec is None:
+                continue
+            cols.append(s)
+            pos.extend(rec["pos"])
+            dirs.extend(rec["dir"])
+            f0.append(rec["f0"])
+            bw.append(rec["bw"])
+            t0.append(rec["t0"])
+        arr = [np.ascontiguousarray(v, dtype=np.float64) for v in (pos, dirs, f0, bw, t0)]
+        c = np.ascontiguousarray(cols, dtype=np.int32)
+        _check(_lib.dgm_set_sources(self.handle, len(cols), c.ctypes.data,
+                                    *[a.ctypes.data for a in arr]))
+
+    def status(self):
+        _check(_lib.dgm_status_check(self.handle))

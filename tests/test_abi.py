@@ -1,0 +1,111 @@
+"""CPU tests of the C ABI: the library builds, loads, exports every function
+declared in include/dgmax.h, and its host-side setup validates inputs.
+No compute call is made (there is no GPU here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_08733_gb300 import build, dgmax
+    build.build()
+    return dgmax.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dgmax.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dgm_plan_create", "dgm_bind", "dgm_rhs", "dgm_advance", "dgm_energy",
+                     "dgm_advance_host", "dgm_set_sources", "dgm_project", "dgm_last_error",
+                     "dgm_plan_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_plan_sizes(lib):
+    from paper_2002_08733_gb300 import dgmax as D
+    xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=1)
+    for p, prec, rs in ((1, "fp64", 8), (3, "fp32", 4), (4, "fp64", 8), (5, "fp32", 4)):
+        pl = D.Plan(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", 1e-3, S=3)
+        N = W.n_modes(p)
+        assert (pl.info.K, pl.info.N, pl.info.S, pl.info.real_size) == (162, N, 3, rs)
+        assert pl.info.bytes_fields == 6 * N * 162 * 3 * rs
+        assert pl.info.bytes_aux == 0 and pl.info.n_pml == 0
+        assert pl.info.bytes_geom % 256 == 0
+
+
+def test_pml_elements_are_those_outside_the_box(lib):
+    from paper_2002_08733_gb300 import dgmax as D
+    xyz, tets = W.kuhn_mesh(4, lo=(-1, -1, -1), hi=(1, 1, 1))
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=10.0)
+    pl = D.Plan(xyz, tets, 1.0, 1.0, 2, "fp32", "upwind", "lsrk4", 1e-3, pml=pml)
+    c = W.centroids(xyz, tets)
+    outside = np.any((c < -0.5) | (c > 0.5), axis=1)
+    assert np.array_equal(pl.pml_elements(), np.nonzero(outside)[0])
+
+
+def test_quad_points_lie_in_their_elements(lib):
+    from paper_2002_08733_gb300 import dgmax as D
+    xyz, tets = W.kuhn_mesh(2, jitter=0.1, seed=3)
+    pl = D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", "upwind", "lsrk4", 1e-3)
+    q = pl.quad_points()
+    st = np.sort(tets, axis=1)
+    for e in (0, 7, 33):
+        V = xyz[st[e]]
+        A = (V[1:] - V[0]).T
+        lam = np.linalg.solve(A, (q[e] - V[0]).T).T
+        assert np.all(lam > -1e-12) and np.all(lam.sum(axis=1) < 1 + 1e-12)
+
+
+@pytest.mark.parametrize("case", ["repeated", "range", "degenerate", "nonmanifold",
+                                  "eps", "order", "leapfrog_upwind", "dt", "columns"])
+def test_invalid_inputs_are_rejected(lib, case):
+    from paper_2002_08733_gb300 import dgmax as D
+    xyz, tets = W.kuhn_mesh(2)
+    kw = dict(eps=1.0, mu=1.0, p=2, precision="fp64", flux="upwind", integrator="lsrk4",
+              dt=1e-3, S=1)
+    expect = D.DgmError
+    if case == "repeated":
+        tets = tets.copy()
+        tets[3, 1] = tets[3, 0]
+    elif case == "range":
+        tets = tets.copy()
+        tets[0, 0] = 10 ** 6
+    elif case == "degenerate":
+        xyz = xyz.copy()
+        xyz[:, 2] = 0.0
+    elif case == "nonmanifold":
+        tets = np.concatenate([tets, tets[:1]])
+    elif case == "eps":
+        kw["eps"] = np.where(np.arange(len(tets)) == 5, -1.0, 1.0)
+    elif case == "order":
+        kw["p"] = 6
+    elif case == "leapfrog_upwind":
+        kw["integrator"] = "leapfrog"
+    elif case == "dt":
+        kw["dt"] = 0.0
+    elif case == "columns":
+        kw["S"] = 0
+    with pytest.raises(expect) as ei:
+        D.Plan(xyz, tets, kw.pop("eps"), kw.pop("mu"), kw.pop("p"), **kw)
+    codes = {"repeated": 2, "range": 2, "degenerate": 2, "nonmanifold": 2, "eps": 1,
+             "order": 3, "leapfrog_upwind": 3, "dt": 1, "columns": 1}
+    assert ei.value.code == codes[case]

@@ -1,0 +1,162 @@
+"""GPU parity of time stepping, energy, projection and the host end-to-end call.
+
+LSRK4 (five 2N-storage stages per step, upwind flux, PML, sources) and
+staggered leapfrog (central flux) trajectories are compared with the oracle
+after several steps; the FP64 energy reduction and the L2 projection of an
+initial field are compared with the oracle's assembled-matrix values.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle_ref import build, rel_err, rel_l2
+from oracle.solver import Solver as OSolver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_2002_08733_gb300 import build as B, dgmax
+    B.build()
+    dgmax.load_library()
+    return dgmax
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_lsrk4_trajectory(D, prec, tol):
+    xyz, tets = W.kuhn_mesh(3, jitter=0.15, seed=21)
+    K, p, S = len(tets), 3, 2
+    eps = W.sphere_material(xyz, tets, (0.5, 0.5, 0.5), 0.3, 4.0, 1.0)
+    dt = W.stable_dt(1 / 3, p)
+    u = W.random_state(K, S, p, seed=22)
+    g = D.Solver(xyz, tets, eps, 1.0, p, prec, "upwind", "lsrk4", dt, S=S)
+    g.set_state(u)
+    g.advance(12, 0.0)
+    got = g.state()
+    o = build(xyz, tets, p, eps, 1.0, "upwind", S=S)
+    ref = o.unpack(o.lsrk4(o.pack(u), 0.0, dt, 12))[0]
+    assert rel_l2(got, ref) < tol
+    assert rel_err(got, ref) < 10 * tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_lsrk4_pml_dipole_trajectory(D, prec, tol):
+    xyz, tets = W.kuhn_mesh(4, (-1, -1, -1), (1, 1, 1))
+    K, p, S = len(tets), 2, 1
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+    srcs = [W.dipole((0.11, -0.07, 0.05), 2.0, 1.0)]
+    dt = W.stable_dt(0.5, p)
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", dt, S=S, pml=pml)
+    g.set_sources(srcs)
+    g.advance(40, 0.0)
+    got = g.state()
+    o = build(xyz, tets, p, 1.0, 1.0, "upwind", pml=pml, S=S, sources=srcs)
+    x = o.lsrk4(np.zeros((o.asm.ndof, S)), 0.0, dt, 40)
+    ref, ref_aux = o.unpack(x)
+    assert np.abs(ref).max() > 1e-4
+    assert rel_l2(got, ref) < tol
+    ga = g.from_device(g.aux[g.current()])
+    assert rel_l2(ga, ref_aux[g.pml_elements()]) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_leapfrog_cavity_trajectory(D, prec, tol):
+    xyz, tets = W.kuhn_mesh(3)
+    K, p = len(tets), 2
+    dt = W.stable_dt(1 / 3, p)
+    u = W.random_state(K, 1, p, seed=31)
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "central", "leapfrog", dt)
+    g.set_state(u)
+    g.leapfrog_start(0.0)
+    g.advance(25, 0.0)
+    got = g.state()
+    o = build(xyz, tets, p, 1.0, 1.0, "central")
+    ref = o.unpack(o.leapfrog(o.pack(u), 0.0, dt, 25))[0]
+    assert rel_l2(got, ref) < tol
+
+
+def test_energy_matches_oracle(D):
+    xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=3)
+    K, p, S = len(tets), 3, 4
+    eps = W.lognormal_material(K, 2.0, 0.3, 4)
+    mu = W.lognormal_material(K, 1.0, 0.2, 5)
+    u = W.random_state(K, S, p, seed=6)
+    g = D.Solver(xyz, tets, eps, mu, p, "fp64", "upwind", "lsrk4", 1e-3, S=S)
+    g.set_state(u)
+    o = build(xyz, tets, p, eps, mu, "upwind", S=S)
+    ref = o.asm.energy(o.pack(u))
+    got = g.energy()
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_central_flux_energy_is_conserved_on_gpu(D):
+    xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=8)
+    p = 3
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, "fp64", "central", "lsrk4", 2e-3)
+    g.set_state(W.random_state(len(tets), 1, p, seed=9))
+    w0 = g.energy()[0]
+    g.advance(50)
+    w1 = g.energy()[0]
+    assert abs(w1 - w0) < 1e-6 * w0     # LSRK4 damping of a skew operator is O(dt^5)
+
+
+def test_upwind_energy_decays_on_gpu(D):
+    xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=8)
+    g = D.Solver(xyz, tets, 1.0, 1.0, 2, "fp32", "upwind", "lsrk4", 2e-3)
+    g.set_state(W.random_state(len(tets), 1, 2, seed=9))
+    w = [g.energy()[0]]
+    for _ in range(5):
+        g.advance(10)
+        w.append(g.energy()[0])
+    assert all(b < a for a, b in zip(w, w[1:]))
+
+
+def test_projection_matches_oracle(D):
+    xyz, tets = W.kuhn_mesh(2, jitter=0.1, seed=12)
+    p = 3
+
+    def field(r):
+        out = np.zeros((len(r), 6))
+        out[:, 2] = np.sin(math.pi * r[:, 0]) * np.sin(math.pi * r[:, 1])
+        out[:, 3] = np.cos(2 * r[:, 2]) * r[:, 0]
+        out[:, 4] = np.exp(-((r - 0.4) ** 2).sum(axis=1) / 0.1)
+        return out
+
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, "fp64", "upwind", "lsrk4", 1e-3)
+    g.project(field)
+    got = g.state()[:, 0]
+    o = build(xyz, tets, p, 1.0, 1.0, "upwind")
+    # the oracle projects with its own quadrature (one degree higher), so the
+    # two agree to the quadrature error of a non-polynomial field
+    ref_e = o.project(lambda r: field(r)[:, 0:3], "E")
+    ref_h = o.project(lambda r: field(r)[:, 3:6], "H")
+    ref = np.concatenate([ref_e, ref_h], axis=1)
+    assert rel_err(got, ref) < 1e-6
+    # on a polynomial field of degree p both are exact
+    poly = lambda r: np.stack([r[:, 0] * r[:, 1], r[:, 2] ** 2, r[:, 0] ** 3, 1 + r[:, 1],
+                               r[:, 2] * r[:, 0], r[:, 1] ** 2 * r[:, 2]], axis=1)
+    g.project(poly)
+    got = g.state()[:, 0]
+    ref = np.concatenate([o.project(lambda r: poly(r)[:, 0:3], "E"),
+                          o.project(lambda r: poly(r)[:, 3:6], "H")], axis=1)
+    assert rel_err(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_host_end_to_end_matches_device_path(D, prec):
+    import torch
+    xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=14)
+    p = 2
+    u = W.random_state(len(tets), 1, p, seed=15)
+    a = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", 1e-3)
+    a.set_state(u)
+    a.advance(7)
+    want = a.fields[a.current()].cpu()
+    b = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", 1e-3)
+    hin = b.to_device(u).cpu().pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    b.advance_host(hin, hout, 7)
+    assert torch.equal(hout, want)
