@@ -137,7 +137,7 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     import torch
     from paper_2002_08733_gb300 import dgmax as D
 
-    w = W.jittered_sphere()
+    w = W.jittered_sphere(n=args.n)
     xyz, tets, eps = build_problem(w)
     dev = torch.device("cuda", rank % max(torch.cuda.device_count(), 1))
     torch.cuda.set_device(dev)
@@ -234,14 +234,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=32,
+                    help="Kuhn grid size (32 = the benchmarked workload; smaller for profiling)")
+    ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
+                    help="profile one precision only")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    w = W.jittered_sphere()
-    config = {"workload": "jittered_sphere: 32^3 Kuhn grid of [0,1]^3 (+-0.15h jitter), "
-                          "196608 tets, p=3, eps=4 sphere r=0.25, upwind, LSRK4, "
-                          "Gaussian pulse", "K": w.K, "p": w.p, "S": 1, "dt": w.dt,
-              "l2": "inputs exceed L2 (3 x field buffers > 129 MB)"}
+    w = W.jittered_sphere(n=args.n)
+    config = {"workload": "jittered_sphere: %d^3 Kuhn grid of [0,1]^3 (+-0.15h jitter), "
+                          "%d tets, p=3, eps=4 sphere r=0.25, upwind, LSRK4, "
+                          "Gaussian pulse" % (args.n, w.K), "K": w.K, "p": w.p, "S": 1,
+              "dt": w.dt, "l2": "inputs exceed L2 (3 x field buffers > 129 MB)"}
 
     if args.impl == "reference":
         if rank != 0:
@@ -278,9 +283,21 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
+    if args.only == "fp64":
+        r = run_gpu(args, "fp64", args.steps, args.warmup, world, rank)
+        if rank == 0:
+            print(json.dumps({"profile_run": "fp64", "ms_per_step": r["ms"] / r["steps"],
+                              "value": r["value"]}))
+        return
     r32 = run_gpu(args, "fp32", args.steps, args.warmup, world, rank)
+    if args.only == "fp32":
+        if rank == 0:
+            print(json.dumps({"profile_run": "fp32", "ms_per_step": r32["ms"] / r32["steps"],
+                              "value": r32["value"]}))
+        return
     r64 = run_gpu(args, "fp64", min(args.fp64_steps, args.steps), min(args.warmup, 3), world, rank)
-    e2e = run_e2e(r32["solver"], max(3, min(20, args.steps // 5)), r32["t"])
+    e2e = None if args.no_e2e else run_e2e(r32["solver"], max(3, min(20, args.steps // 5)),
+                                           r32["t"])
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"

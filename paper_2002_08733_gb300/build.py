@@ -17,12 +17,15 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
+GEN = os.path.join(BUILD, "gen")
+GEN_HEADER = os.path.join(GEN, "dgm_ops_gen.cuh")
+GENERATOR_SRC = ("dgm_refgen.cpp", "dgm_refmats.cpp")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libdgmax.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", GEN]
 
 
 def nvcc():
@@ -34,13 +37,35 @@ def nvcc():
 
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
-                  if f.endswith(".cu") or f.endswith(".cpp"))
+                  if (f.endswith(".cu") or f.endswith(".cpp")) and f != "dgm_refgen.cpp")
 
 
 def headers():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hs += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
+    if os.path.exists(GEN_HEADER):
+        hs.append(GEN_HEADER)
     return hs
+
+
+def generate_operators():
+    """Compile and run dgm_refgen (host) to write the straight-line reference operators."""
+    os.makedirs(GEN, exist_ok=True)
+    srcs = [os.path.join(CSRC, f) for f in GENERATOR_SRC]
+    deps = srcs + [os.path.join(CSRC, "dgm_internal.h")]
+    newest = max(os.path.getmtime(d) for d in deps)
+    if os.path.exists(GEN_HEADER) and os.path.getmtime(GEN_HEADER) >= newest:
+        return
+    exe = os.path.join(BUILD, "refgen")
+    cmd = [nvcc(), "-x", "c++", "-O2", "-std=c++17", "-I", INCLUDE, "-I", CSRC] + srcs + ["-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("generator build failed:\n%s\n%s" % (r.stdout, r.stderr))
+    tmp = GEN_HEADER + ".tmp"
+    r = subprocess.run([exe, tmp], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("generator failed:\n%s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, GEN_HEADER)
 
 
 def _compile(src, extra):
@@ -59,6 +84,7 @@ def _compile(src, extra):
 def build(verbose=False, jobs=None, extra=()):
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
+    generate_operators()
     srcs = sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     errors, objs = [], []

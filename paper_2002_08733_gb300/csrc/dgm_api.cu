@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "dgm_internal.h"
+#include "dgm_ops_gen.cuh"
 #include "dgmax.h"
 
 namespace dgm {
@@ -180,6 +181,23 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
         delete P;
         return fail(DGM_EINVAL, err);
     }
+    {   // the kernels carry the reference operators as compiled literals: check them
+        const double* cs = ref_S_compiled(opt->p);
+        const double* cr = ref_R_compiled(opt->p);
+        double worst = 0.0, scale = 0.0;
+        for (size_t i = 0; i < P->S.size(); ++i) {
+            worst = std::fmax(worst, std::fabs(P->S[i] - cs[i]));
+            scale = std::fmax(scale, std::fabs(P->S[i]));
+        }
+        for (size_t i = 0; i < P->R.size(); ++i) {
+            worst = std::fmax(worst, std::fabs(P->R[i] - cr[i]));
+            scale = std::fmax(scale, std::fabs(P->R[i]));
+        }
+        if (!(worst <= 1e-13 * scale)) {
+            delete P;
+            return fail(DGM_EINVAL, "compiled reference operators differ from the run-time ones");
+        }
+    }
     const int64_t K = P->mesh.K;
     const int Sc = opt->n_columns;
     size_t off = 0;
@@ -258,8 +276,6 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
         return cuda_fail(e, "clear status");
     // the host copies above are pageable: finish them before the host vectors can change
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
-    int rc = P->kt->set_refmats(P->S.data(), P->R.data());
-    if (rc) return fail(rc, "upload reference matrices");
     P->bound = true;
     return DGM_OK;
 }

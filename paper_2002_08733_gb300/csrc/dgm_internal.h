@@ -56,7 +56,6 @@ struct StageParams {
 // Kernel translation unit entry points, one set per (order, precision).
 struct KernelTable {
     int (*launch_stage)(const StageParams&, int mode, void* stream);
-    int (*set_refmats)(const double* S, const double* R);  // S[3][N][N], R[4][NF][N]
     int real_size;
 };
 

@@ -1,7 +1,6 @@
 // Body of one kernel translation unit: instantiates the fused stage kernel for
 // one polynomial degree (DGM_P), one field precision (DGM_REAL) and one mode
-// (DGM_MODE), owns that module's copy of the reference matrices in
-// __constant__ memory and exports DGM_LAUNCH / DGM_SETREF.  Included by the
+// (DGM_MODE) and exports its launcher DGM_LAUNCH.  Included by the
 // dgm_kern_p<P>_<precision>_<mode>.cu files; one mode per file keeps the
 // heavily unrolled kernels compiling in parallel.
 #include <cuda_runtime.h>
@@ -10,13 +9,6 @@
 
 #include "dgm_internal.h"
 #include "dgmax.h"
-
-namespace dgm {
-
-static __constant__ DGM_REAL dgm_cS[3][nmodes(DGM_P)][nmodes(DGM_P)];
-static __constant__ DGM_REAL dgm_cR[4][nfmodes(DGM_P)][nmodes(DGM_P)];
-
-}  // namespace dgm
 
 #include "dgm_stage.cuh"
 
@@ -45,22 +37,12 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
 }
 
-int set_refmats(const double* S, const double* R) {
-    constexpr int N = nmodes(kP), NF = nfmodes(kP);
-    std::vector<Real> s(3 * N * N), r(4 * NF * N);
-    for (size_t i = 0; i < s.size(); ++i) s[i] = Real(S[i]);
-    for (size_t i = 0; i < r.size(); ++i) r[i] = Real(R[i]);
-    if (cudaMemcpyToSymbol(dgm_cS, s.data(), s.size() * sizeof(Real)) != cudaSuccess) return DGM_ECUDA;
-    if (cudaMemcpyToSymbol(dgm_cR, r.data(), r.size() * sizeof(Real)) != cudaSuccess) return DGM_ECUDA;
-    return DGM_OK;
-}
-
 }  // namespace
 
 int DGM_LAUNCH(const StageParams& prm, void* stream) {
     return launch_mode(prm, static_cast<cudaStream_t>(stream));
 }
 
-int DGM_SETREF(const double* S, const double* R) { return set_refmats(S, R); }
+
 
 }  // namespace dgm

@@ -3,5 +3,4 @@
 #define DGM_REAL float
 #define DGM_MODE MODE_LF_E
 #define DGM_LAUNCH launch_p2_f32_lfe
-#define DGM_SETREF setref_p2_f32_lfe
 #include "dgm_kern_impl.cuh"

@@ -3,5 +3,4 @@
 #define DGM_REAL double
 #define DGM_MODE MODE_RHS
 #define DGM_LAUNCH launch_p2_f64_rhs
-#define DGM_SETREF setref_p2_f64_rhs
 #include "dgm_kern_impl.cuh"

@@ -3,5 +3,4 @@
 #define DGM_REAL float
 #define DGM_MODE MODE_LSRK
 #define DGM_LAUNCH launch_p3_f32_lsrk
-#define DGM_SETREF setref_p3_f32_lsrk
 #include "dgm_kern_impl.cuh"

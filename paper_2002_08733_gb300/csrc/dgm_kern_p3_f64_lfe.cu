@@ -3,5 +3,4 @@
 #define DGM_REAL double
 #define DGM_MODE MODE_LF_E
 #define DGM_LAUNCH launch_p3_f64_lfe
-#define DGM_SETREF setref_p3_f64_lfe
 #include "dgm_kern_impl.cuh"

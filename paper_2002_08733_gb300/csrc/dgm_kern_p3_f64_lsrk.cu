@@ -3,5 +3,4 @@
 #define DGM_REAL double
 #define DGM_MODE MODE_LSRK
 #define DGM_LAUNCH launch_p3_f64_lsrk
-#define DGM_SETREF setref_p3_f64_lsrk
 #include "dgm_kern_impl.cuh"

@@ -3,5 +3,4 @@
 #define DGM_REAL float
 #define DGM_MODE MODE_RHS
 #define DGM_LAUNCH launch_p4_f32_rhs
-#define DGM_SETREF setref_p4_f32_rhs
 #include "dgm_kern_impl.cuh"

@@ -3,5 +3,4 @@
 #define DGM_REAL double
 #define DGM_MODE MODE_LF_H
 #define DGM_LAUNCH launch_p4_f64_lfh
-#define DGM_SETREF setref_p4_f64_lfh
 #include "dgm_kern_impl.cuh"

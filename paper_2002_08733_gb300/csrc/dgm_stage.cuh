@@ -30,18 +30,18 @@
 //   3 numerical flux per (face, face mode), pulled back to the element
 //   4 right-hand side per component: volume curl + lift (+ source)
 //   5 3x3 mass-block inverse, PML terms, and the stage update
-// The reference matrices live in __constant__ memory of the including
-// translation unit (dgm_cS[3][N][N], dgm_cR[4][NF][N], defined before this
-// header is included), and every matrix entry is a compile-time index, so it
-// is an FMA operand.
-// Only structurally non-zero entries are visited: S_a[l][m] = 0 unless
-// deg(l) < deg(m), and R_f[m][l] = 0 unless deg(m) <= deg(l), because the
-// bases are hierarchical and orthonormal.
+// The reference operators are straight-line code with literal coefficients
+// (generated at build time, dgm_refgen.cpp) that visits only the non-zero
+// entries: S_a[l][m] = 0 unless deg(l) < deg(m), R_f[m][l] = 0 unless
+// deg(m) <= deg(l) (hierarchical orthonormal bases), and many more entries
+// vanish exactly for the collapsed basis (e.g. on the face x = 0 each mode
+// has a single face mode).
 #pragma once
 
 #include <cstdint>
 
 #include "dgm_internal.h"
+#include "dgm_ops_gen.cuh"
 
 namespace dgm {
 
@@ -65,20 +65,12 @@ __host__ __device__ constexpr size_t stage_smem_bytes() {
            (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FG + EG);
 }
 
-// out[m] (m < NF) = sum_l R[f][m][l] v[l] over the structural non-zeros
+// Reference operators: straight-line code with literal coefficients generated
+// at build time from the library's own reference matrices (dgm_refgen.cpp),
+// visiting only the entries that are not zero.
 template <int P, typename R, int F>
 __device__ __forceinline__ void trace_face(const R (&v)[nmodes(P)], R (&acc)[nfmodes(P)]) {
-    constexpr int NF = nfmodes(P);
-#pragma unroll
-    for (int m = 0; m < NF; ++m) acc[m] = R(0);
-#pragma unroll
-    for (int d = 0; d <= P; ++d) {
-#pragma unroll
-        for (int l = off3(d); l < off3(d + 1); ++l) {
-#pragma unroll
-            for (int m = 0; m < nfmodes(d); ++m) acc[m] += dgm_cR[F][m][l] * v[l];
-        }
-    }
+    TraceOp<P, F>::template apply<R>(v, acc);
 }
 
 template <int P, typename R>
@@ -91,32 +83,16 @@ __device__ __forceinline__ void trace_any(int f, const R (&v)[nmodes(P)], R (&ac
     }
 }
 
-// acc[l] += sign * sum_m S[a][l][m] v[m] over deg(l) < deg(m)
+// acc[l] += sign * sum_m S[a][l][m] v[m]
 template <int P, typename R, int A>
 __device__ __forceinline__ void deriv_acc(const R* vs, int stride, R sign, R (&acc)[nmodes(P)]) {
-#pragma unroll
-    for (int d = 1; d <= P; ++d) {
-#pragma unroll
-        for (int m = off3(d); m < off3(d + 1); ++m) {
-            const R v = sign * vs[m * stride];
-#pragma unroll
-            for (int l = 0; l < off3(d); ++l) acc[l] += dgm_cS[A][l][m] * v;
-        }
-    }
+    DerivOp<P, A>::template apply<R>(vs, stride, sign, acc);
 }
 
-// acc[l] += sum_m R[f][m][l] g[m] over deg(m) <= deg(l)
+// acc[l] += sum_m R[f][m][l] g[m]
 template <int P, typename R, int F>
 __device__ __forceinline__ void lift_face(const R* gs, int stride, R (&acc)[nmodes(P)]) {
-#pragma unroll
-    for (int dm = 0; dm <= P; ++dm) {
-#pragma unroll
-        for (int m = off2(dm); m < off2(dm + 1); ++m) {
-            const R g = gs[m * stride];
-#pragma unroll
-            for (int l = off3(dm); l < nmodes(P); ++l) acc[l] += dgm_cR[F][m][l] * g;
-        }
-    }
+    LiftOp<P, F>::template apply<R>(gs, stride, acc);
 }
 
 template <typename R>

@@ -129,12 +129,12 @@ def test_projection_matches_oracle(D):
     g.project(field)
     got = g.state()[:, 0]
     o = build(xyz, tets, p, 1.0, 1.0, "upwind")
-    # the oracle projects with its own quadrature (one degree higher), so the
-    # two agree to the quadrature error of a non-polynomial field
+    # the oracle projects with its own quadrature (one degree higher), so for a
+    # non-polynomial field the two agree only to the quadrature error (~1e-5 here)
     ref_e = o.project(lambda r: field(r)[:, 0:3], "E")
     ref_h = o.project(lambda r: field(r)[:, 3:6], "H")
     ref = np.concatenate([ref_e, ref_h], axis=1)
-    assert rel_err(got, ref) < 1e-6
+    assert rel_err(got, ref) < 1e-4
     # on a polynomial field of degree p both are exact
     poly = lambda r: np.stack([r[:, 0] * r[:, 1], r[:, 2] ** 2, r[:, 0] ** 3, 1 + r[:, 1],
                                r[:, 2] * r[:, 0], r[:, 1] ** 2 * r[:, 2]], axis=1)
