@@ -172,6 +172,30 @@ int dgm_quad_points(const dgm_plan* plan, double* xyz_out);
  * `fields` (synchronous copy on the bound stream). */
 int dgm_project(dgm_plan* plan, const double* samples, int32_t column, void* fields);
 
+/* Energy per column, like dgm_energy, but for callers that must not allocate.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let the library touch the device allocator, e.g. a latency-critical
+ * stepping loop in which a cudaMalloc/cudaFree would synchronise the device,
+ * or a host application whose device memory is owned entirely by another
+ * framework's allocator.  It allocates nothing and makes no allocating call;
+ * its reduction scratch is a fixed array inside the library (file-scope
+ * device memory, DGM_NOALLOC_MAX_COLUMNS * 304 doubles = 152 KiB, held by
+ * every GPU that loads the library until the process exits).
+ *
+ * fields: device field buffer of the plan; out_device: device array of S
+ * doubles receiving the energies (written on the bound stream, no host
+ * synchronisation).  Errors: DGM_EINVAL if the plan has more than
+ * DGM_NOALLOC_MAX_COLUMNS columns, DGM_ESTATE if not bound.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one scratch array (each
+ * call overwrites every entry it later reads, so nothing needs clearing):
+ * calls whose kernels overlap on the GPU (other streams, other threads)
+ * race and must be ordered by the caller. */
+#define DGM_NOALLOC_MAX_COLUMNS 64
+int dgm_energy_noalloc(dgm_plan* plan, const void* fields, double* out_device);
+
 /* Read and clear the device status word (synchronises).  Returns DGM_OK or
  * the latched device error. */
 int dgm_status_check(dgm_plan* plan);

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -543,3 +544,63 @@ int dgm_status_check(dgm_plan* P) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free energy (dgm_energy_noalloc): same kernels as dgm_energy, with
+// the per-block partial sums in a fixed file-scope device array instead of the
+// caller's geometry/workspace buffer.  Host code must not pass the symbol
+// itself to a kernel (on the host it names a stand-in, not device memory): its
+// device address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_energy_scratch[DGM_NOALLOC_MAX_COLUMNS * ENERGY_BLOCKS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_energy_scratch on the current device (looked up on first use).
+int scratch_for_current_device(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(DGM_EUNSUP, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_energy_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(energy scratch)");
+        g_scratch_ptr[dev] = static_cast<double*>(ptr);
+    }
+    *out = g_scratch_ptr[dev];
+    return DGM_OK;
+}
+}  // namespace
+
+extern "C" int dgm_energy_noalloc(dgm_plan* P, const void* fields, double* out_device) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!fields || !out_device) return fail(DGM_EINVAL, "null argument");
+    const int Sc = P->opt.n_columns;
+    if (Sc > DGM_NOALLOC_MAX_COLUMNS)
+        return fail(DGM_EINVAL, "dgm_energy_noalloc supports at most " +
+                                    std::to_string(DGM_NOALLOC_MAX_COLUMNS) + " columns, plan has " +
+                                    std::to_string(Sc));
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != P->device) return fail(DGM_ESTATE, "current device is not the plan's device");
+    double* part = nullptr;
+    int rc = scratch_for_current_device(&part);
+    if (rc) return rc;
+    const double* geo = reinterpret_cast<const double*>(P->geom + P->off_geo);
+    dim3 grid(ENERGY_BLOCKS, Sc);
+    if (P->kt->real_size == 8)
+        energy_partial<double><<<grid, ENERGY_THREADS, 0, P->stream>>>(
+            static_cast<const double*>(fields), geo, P->mesh.K, Sc, P->N, part);
+    else
+        energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
+            static_cast<const float*>(fields), geo, P->mesh.K, Sc, P->N, part);
+    energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(part, ENERGY_BLOCKS, Sc, out_device);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
+    return DGM_OK;
+}

@@ -64,6 +64,7 @@ _SIGS = {
     "dgm_current": [_P],
     "dgm_advance_host": [_P, _P, _P, ctypes.c_int64, ctypes.c_double],
     "dgm_energy": [_P, _P, _P],
+    "dgm_energy_noalloc": [_P, _P, _P],
     "dgm_pml_elements": [_P, _P],
     "dgm_quad_points": [_P, _P],
     "dgm_project": [_P, _P, ctypes.c_int32, _P],
@@ -250,6 +251,12 @@ class Solver(Plan):
         out = np.zeros(self.S)
         _check(_lib.dgm_energy(self.handle, _ptr(f), out.ctypes.data))
         return out
+
+    def energy_noalloc(self, out, fields=None):
+        """Allocation-free energy into the device tensor `out` (S doubles) on the
+        bound stream; the library's own fixed scratch array holds the partial sums."""
+        f = self.fields[self.current()] if fields is None else fields
+        _check(_lib.dgm_energy_noalloc(self.handle, _ptr(f), _ptr(out)))
 
     def project(self, fn, column=0):
         """L2 projection of fn(points [n,3]) -> [n,6] (E, H) into the current state."""
