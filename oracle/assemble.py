@@ -92,8 +92,9 @@ class Assembly:
         self.N = self.basis.N
         self.K = mesh.K
         self.n3 = 3 * self.N
-        self.eps = np.asarray(eps, dtype=np.float64) * np.ones(self.K)
-        self.mu = np.asarray(mu, dtype=np.float64) * np.ones(self.K)
+        # eps/mu may be complex (complex-step derivatives in oracle.adjoint)
+        self.eps = np.asarray(eps) * np.ones(self.K)
+        self.mu = np.asarray(mu) * np.ones(self.K)
         if flux not in ("central", "upwind"):
             raise ValueError(flux)
         self.flux = flux
@@ -253,6 +254,7 @@ class Assembly:
         self.Kmat = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows),
                                                            np.concatenate(cols))),
                                   shape=(nblk * R * n3, self.ndof))
+        self.Kmat.sum_duplicates()
         # element mass blocks per field block: eps M1, mu M1, M1, M1 (dense inverses)
         er, mr = self.eps[self.rows], self.mu[self.rows]
         scale = [er, mr, np.ones(R), np.ones(R)][:nblk]

@@ -94,7 +94,7 @@ class Solver:
     # -- operator --------------------------------------------------------------
     def source_vector(self, t):
         a = self.asm
-        f = np.zeros((a.Kmat.shape[0], self.S))
+        f = np.zeros((a.Kmat.shape[0], self.S), dtype=np.result_type(a.Kmat.dtype, np.float64))
         for s, T, w, rec in self.src:
             if a.pos[T] < 0:
                 continue
