@@ -181,6 +181,47 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     return out
 
 
+def run_pml(precision, steps, warmup, n=40):
+    """Dipole-in-PML workload: [-1,1]^3 on an n^3 Kuhn grid (384,000 tets at n=40),
+    p=4, PML 0.25 thick with quadratic profile and sigma_max=40, z-directed
+    dipole, upwind flux, LSRK4, starting from rest.  Returns timing and the
+    algorithmic bytes of one step (fields plus PML auxiliaries)."""
+    import torch
+    from paper_2002_08733_gb300 import dgmax as D
+    w = W.dipole_pml(n=n)
+    xyz, tets = w.mesh()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    g = D.Solver(xyz, tets, 1.0, 1.0, w.p, precision, w.flux, w.integrator, w.dt, device=dev,
+                 stream=stream, pml=w.pml)
+    g.set_sources(w.extra["sources"])
+    t = 0.0
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.advance(1, t)
+            t += w.dt
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            g.advance(1, t)
+            t += w.dt
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        g.status()
+    dofs = 6 * g.N * g.K
+    rs = g.info.real_size
+    field = 6 * g.N * g.K * rs
+    aux = 6 * g.N * g.npml * rs
+    geo = g.K * (16 * 8 + 4 * 4 + 4)
+    step_bytes = (3 * field + 3 * aux + geo) + 4 * (4 * field + 4 * aux + geo)
+    return dict(value=dofs * steps / (ms * 1e-3), ms_per_step=ms / steps, steps=steps, K=g.K,
+                N=g.N, n_pml=g.npml, bytes_per_step=step_bytes,
+                hbm_frac=step_bytes / (ms / steps * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0))
+
+
 def run_e2e(g, steps, t0):
     """End-to-end: per step, pinned host state -> device, one step, device -> host."""
     import torch
@@ -239,6 +280,8 @@ def main():
                     help="Kuhn grid size (32 = the benchmarked workload; smaller for profiling)")
     ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
                     help="profile one precision only")
+    ap.add_argument("--no-pml", action="store_true", help="skip the p=4 dipole-in-PML workload")
+    ap.add_argument("--pml-steps", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,6 +371,12 @@ def main():
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
     }
+    if not args.no_pml and world == 1:
+        p32 = run_pml("fp32", args.pml_steps, 3)
+        p64 = run_pml("fp64", max(2, args.pml_steps // 5), 1)
+        line["p4_pml"] = {"workload": "dipole_pml: [-1,1]^3, 40^3 Kuhn grid, 384000 tets, p=4, "
+                                      "PML 0.25 sigma_max=40, z dipole, upwind, LSRK4",
+                          "fp32": p32, "fp64": p64, "fp32_over_fp64": p32["value"] / p64["value"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, _ = cpu_reference(seconds_budget=15.0)
         line["cpu_baseline"] = base

@@ -69,7 +69,7 @@ typedef struct {
     int32_t flux;       /* DGM_CENTRAL or DGM_UPWIND */
     int32_t integrator; /* DGM_LEAPFROG or DGM_LSRK4 */
     int32_t n_columns;  /* S >= 1 independent problems (sources) sharing the mesh */
-    int32_t reserved;
+    int32_t max_receivers; /* capacity for dgm_set_receivers (0: none) */
     double dt;          /* time step */
 } dgm_options;
 
@@ -129,6 +129,17 @@ int dgm_bind(dgm_plan* plan, void* geom, void* fields0, void* fields1, void* res
 int dgm_set_sources(dgm_plan* plan, int32_t n, const int32_t* column, const double* pos,
                     const double* dir, const double* f0, const double* bw, const double* t0);
 
+/* Receivers: points at which dgm_sample_receivers evaluates E.  n <= the
+ * plan's max_receivers; pos: host [n][3].  Each point is located in the
+ * lowest-index element containing it.  Requires a bound plan (uploads and
+ * synchronises).  Errors: DGM_EINVAL (too many, or a point outside the mesh). */
+int dgm_set_receivers(dgm_plan* plan, int32_t n, const double* pos);
+
+/* Physical E at the receivers for every column, E(r) = A^-T sum_l u_l phi_l(r_hat)
+ * (Eq. (mapped_eh)): out_device[s][r][3] doubles (device), computed from the
+ * device field buffer `fields` on the bound stream (asynchronous). */
+int dgm_sample_receivers(dgm_plan* plan, const void* fields, double* out_device);
+
 /* One evaluation of the semi-discrete right-hand side at time t (the hot
  * path of one stage: reference-curl volume term, face traces, numerical flux,
  * lift, 3x3 mass-block inverse, PML terms, sources):
@@ -144,6 +155,51 @@ int dgm_leapfrog_start(dgm_plan* plan, double t0);
 /* Advance the bound state n_steps time steps from time t0 (asynchronous).
  * LSRK4 ping-pongs between fields0 and fields1 (and aux0/aux1). */
 int dgm_advance(dgm_plan* plan, int64_t n_steps, double t0);
+
+/* Batched advance of several independent problems (the batching pattern of
+ * many sources and uneven problems): a batch groups bound LSRK4 plans of any
+ * order/precision; dgm_batch_advance advances every member by n_steps using
+ * one CUDA graph launch per two time steps, inside which the members' stage
+ * kernels run concurrently on forked streams (each member keeps its own time
+ * step, sources and buffers).  The graph is captured at creation.  Member
+ * times live in device memory (a slot of each member's geometry buffer), so
+ * sources see the right time in every replay.  Ordering: the batch waits for
+ * work already queued on the members' bound streams and the members' streams
+ * wait for the batch.  stream: the caller's stream (cudaStream_t, may be 0),
+ * ordered before and after each advance; the graph itself runs on a stream
+ * the batch owns.  Errors: DGM_EINVAL (no members, unbound or non-LSRK4 member,
+ * duplicate member), DGM_ECUDA. */
+typedef struct dgm_batch dgm_batch;
+int dgm_batch_create(dgm_batch** out, dgm_plan* const* members, int32_t n, void* stream);
+/* t0: host array of n start times (NULL: all 0).  Asynchronous. */
+int dgm_batch_advance(dgm_batch* batch, int64_t n_steps, const double* t0);
+void dgm_batch_destroy(dgm_batch* batch);
+
+/* Replace the per-element materials of a plan (host arrays [K]); uploads if
+ * bound (synchronous).  The geometry and everything else are kept. */
+int dgm_set_materials(dgm_plan* plan, const double* eps, const double* mu);
+
+/* Discrete adjoint of LSRK4 time stepping with receivers (gradient of a loss
+ * of the receiver records with respect to per-element eps and mu).
+ *
+ * dgm_forward_record advances the bound state n_steps from time t0 (like
+ * dgm_advance), writes the receiver records after every step to
+ * records_device [n_steps][S][R][3] (doubles, R = receivers set) and keeps
+ * ceil(sqrt(n_steps)) checkpoints in `workspace`.  dgm_adjoint then runs the
+ * adjoint backwards in time from dL/drecords (device, same layout as the
+ * records): each checkpoint segment is recomputed forward, each step's five
+ * stage inputs are recomputed from its start, and the transposed stage
+ * kernels accumulate the gradient per column in FP64; deps_device and
+ * dmu_device (doubles [K]) receive dL/d eps_T and dL/d mu_T summed over
+ * columns.  workspace: device memory of dgm_adjoint_workspace bytes,
+ * 256-byte aligned, owned by the caller, shared by the two calls.  The
+ * adjoint stage matches the discrete transpose of the forward stage exactly
+ * (same reference operators, flux, PML, sources). */
+int dgm_adjoint_workspace(const dgm_plan* plan, int64_t n_steps, size_t* bytes);
+int dgm_forward_record(dgm_plan* plan, int64_t n_steps, double t0, double* records_device,
+                       void* workspace);
+int dgm_adjoint(dgm_plan* plan, int64_t n_steps, double t0, const double* drecords_device,
+                void* workspace, double* deps_device, double* dmu_device);
 
 /* Index (0 or 1) of the bound field/aux buffer that holds the current state. */
 int dgm_current(const dgm_plan* plan);

@@ -3,6 +3,7 @@
 // energy reduction, point sources and L2 projection of initial values.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,7 @@ static const double LSRK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
                                  2802321613138.0 / 2924317926251.0};
 
 constexpr int ENERGY_BLOCKS = 304;   // 2 per SM
+constexpr int REC_HDR = 4;           // receiver record: [elem, 0, 0, 0, W[3][3N]]
 constexpr int ENERGY_THREADS = 256;
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -63,7 +65,8 @@ struct dgm_plan {
     bool has_pml = false;
     // geometry buffer layout (byte offsets)
     size_t off_geo = 0, off_nbr = 0, off_pml = 0, off_src = 0, off_part = 0, off_status = 0,
-           bytes_geom = 0;
+           off_rec = 0, off_time = 0, bytes_geom = 0;
+    int n_rec = 0;
     std::vector<double> src_host;   // S * (SRC_HDR + 3N)
     bool have_src = false;
     // bound state
@@ -137,6 +140,26 @@ __global__ void energy_final(const double* __restrict__ part, int nblk, int S, d
     double acc = 0.0;
     for (int b = 0; b < nblk; ++b) acc += part[int64_t(s) * nblk + b];
     out[s] = acc;
+}
+
+// E at receiver points: out[s][r][c] = sum_{j,l} W_r[c][j N + l] u[(j N + l)][e_r S + s],
+// W_r[c][j N + l] = A^-T[c][j] phi_l(r_hat)
+template <typename R>
+__global__ void sample_receivers(const R* __restrict__ u, const double* __restrict__ rec, int nrec,
+                                 int64_t K, int S, int N, double* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(nrec) * S) return;
+    const int r = int(i / S), s = int(i % S);
+    const double* w = rec + int64_t(r) * (REC_HDR + 9 * N);
+    const int64_t e = int64_t(w[0]);
+    const int64_t C = K * S;
+    const int64_t col = e * S + s;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int jl = 0; jl < 3 * N; ++jl) {
+        const double v = double(u[int64_t(jl) * C + col]);
+        for (int c = 0; c < 3; ++c) acc[c] += w[REC_HDR + c * 3 * N + jl] * v;
+    }
+    for (int c = 0; c < 3; ++c) out[(int64_t(s) * nrec + r) * 3 + c] = acc[c];
 }
 
 // ---------------------------------------------------------------------------
@@ -214,6 +237,14 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
     off = align256(off + sizeof(double) * (size_t(Sc) * ENERGY_BLOCKS + Sc));
     P->off_status = off;
     off = align256(off + 64);
+    P->off_time = off;   // device clock used by graph replays (dgm_batch)
+    off = align256(off + 64);
+    if (opt->max_receivers < 0) {
+        delete P;
+        return fail(DGM_EINVAL, "max_receivers must be >= 0");
+    }
+    P->off_rec = off;
+    off = align256(off + sizeof(double) * size_t(opt->max_receivers) * (REC_HDR + 9 * P->N));
     P->bytes_geom = off;
     P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
     for (int s = 0; s < Sc; ++s) P->src_host[size_t(s) * (SRC_HDR + 3 * P->N)] = -1.0;
@@ -349,6 +380,74 @@ int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double*
     if (e != cudaSuccess) return cuda_fail(e, "upload sources");
     if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "source sync");
     return DGM_OK;
+}
+
+// lowest-index element containing r (barycentric >= -1e-12); fills reference coordinates
+static int64_t locate_point(const dgm_plan* P, const double* r, double xr[3]) {
+    const int64_t K = P->mesh.K;
+    for (int64_t e = 0; e < K; ++e) {
+        const double* V = &P->mesh.verts[12 * e];
+        double d[3] = {r[0] - V[0], r[1] - V[1], r[2] - V[2]};
+        double lam[3];
+        for (int a = 0; a < 3; ++a)   // r_hat = A^-1 (r - v0), A^-1[a][c] = A^-T[c][a]
+            lam[a] = P->mesh.geo[(G_AIT + 3 * 0 + a) * K + e] * d[0] +
+                     P->mesh.geo[(G_AIT + 3 * 1 + a) * K + e] * d[1] +
+                     P->mesh.geo[(G_AIT + 3 * 2 + a) * K + e] * d[2];
+        const double tol = 1e-12;
+        if (lam[0] >= -tol && lam[1] >= -tol && lam[2] >= -tol && lam[0] + lam[1] + lam[2] <= 1 + tol) {
+            for (int a = 0; a < 3; ++a) xr[a] = lam[a];
+            return e;
+        }
+    }
+    return -1;
+}
+
+int dgm_set_receivers(dgm_plan* P, int32_t n, const double* pos) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (n < 0 || n > P->opt.max_receivers || (n > 0 && !pos))
+        return fail(DGM_EINVAL, "receiver count exceeds max_receivers or null positions");
+    const int N = P->N;
+    const int64_t K = P->mesh.K;
+    const size_t rec = REC_HDR + 9 * N;
+    std::vector<double> host(size_t(n) * rec, 0.0), phi(N);
+    for (int i = 0; i < n; ++i) {
+        double xr[3];
+        const int64_t e = locate_point(P, pos + 3 * i, xr);
+        if (e < 0) return fail(DGM_EINVAL, "receiver point outside the mesh");
+        double* w = &host[i * rec];
+        w[0] = double(e);
+        ref_basis_values(P->opt.p, xr, phi.data());
+        for (int c = 0; c < 3; ++c)
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < N; ++l)
+                    w[REC_HDR + c * 3 * N + j * N + l] = P->mesh.geo[(G_AIT + 3 * c + j) * K + e] * phi[l];
+    }
+    P->n_rec = n;
+    if (n == 0) return DGM_OK;
+    cudaError_t e = cudaMemcpyAsync(P->geom + P->off_rec, host.data(), sizeof(double) * host.size(),
+                                    cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload receivers");
+    if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "receiver sync");
+    return DGM_OK;
+}
+
+int dgm_sample_receivers(dgm_plan* P, const void* fields, double* out_device) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!fields || !out_device) return fail(DGM_EINVAL, "null argument");
+    if (P->n_rec == 0) return DGM_OK;
+    const int64_t n = int64_t(P->n_rec) * P->opt.n_columns;
+    const double* rec = reinterpret_cast<const double*>(P->geom + P->off_rec);
+    const unsigned grid = unsigned((n + 127) / 128);
+    if (P->kt->real_size == 8)
+        sample_receivers<double><<<grid, 128, 0, P->stream>>>(static_cast<const double*>(fields), rec,
+                                                              P->n_rec, P->mesh.K, P->opt.n_columns,
+                                                              P->N, out_device);
+    else
+        sample_receivers<float><<<grid, 128, 0, P->stream>>>(static_cast<const float*>(fields), rec,
+                                                             P->n_rec, P->mesh.K, P->opt.n_columns,
+                                                             P->N, out_device);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "receiver kernel launch");
 }
 
 int dgm_rhs(dgm_plan* P, const void* fields, const void* aux, void* dfields, void* daux, double t) {
@@ -604,3 +703,416 @@ extern "C" int dgm_energy_noalloc(dgm_plan* P, const void* fields, double* out_d
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
     return DGM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched advance through a captured CUDA graph (dgm_batch_*).
+__global__ void advance_clock(double* t, double dt) { *t += dt; }
+
+struct dgm_batch {
+    std::vector<dgm_plan*> members;
+    cudaStream_t user = nullptr;     // caller's stream (may be the legacy default stream)
+    cudaStream_t stream = nullptr;   // the batch's own stream: graphs are captured/launched here
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_release(dgm_batch* B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    for (auto s : B->side) cudaStreamDestroy(s);
+    for (auto e : B->join) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->stream) cudaStreamDestroy(B->stream);
+    delete B;
+}
+
+// one LSRK4 step of member P on stream st with the device clock
+static int member_step(dgm_plan* P, cudaStream_t st) {
+    StageParams prm;
+    stage_params(P, prm);
+    double* clock = reinterpret_cast<double*>(P->geom + P->off_time);
+    prm.tdev = clock;
+    const double dt = P->opt.dt;
+    for (int k = 0; k < 5; ++k) {
+        prm.u = P->fields[P->cur];
+        prm.u_out = P->fields[1 - P->cur];
+        prm.res = P->res;
+        prm.aux = P->aux[P->cur];
+        prm.aux_out = P->aux[1 - P->cur];
+        prm.aux_res = P->aux_res;
+        prm.t = LSRK_C[k] * dt;
+        prm.a = LSRK_A[k];
+        prm.b = LSRK_B[k];
+        int rc = P->kt->launch_stage(prm, MODE_LSRK, st);
+        if (rc) return rc;
+        P->cur = 1 - P->cur;
+    }
+    advance_clock<<<1, 1, 0, st>>>(clock, dt);
+    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+}
+
+extern "C" int dgm_batch_create(dgm_batch** out, dgm_plan* const* members, int32_t n, void* stream) {
+    if (!out || !members || n < 1) return fail(DGM_EINVAL, "empty batch");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!members[i] || !members[i]->bound) return fail(DGM_EINVAL, "batch member not bound");
+        if (members[i]->opt.integrator != DGM_LSRK4) return fail(DGM_EINVAL, "batch members must use LSRK4");
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return fail(DGM_EINVAL, "duplicate batch member");
+    }
+    dgm_batch* B = new dgm_batch();
+    B->members.assign(members, members + n);
+    B->user = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        batch_release(B);
+        return cuda_fail(e, "stream create");
+    }
+    if ((e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming)) != cudaSuccess) {
+        batch_release(B);
+        return cuda_fail(e, "event create");
+    }
+    for (int i = 0; i < n; ++i) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            batch_release(B);
+            return cuda_fail(e, "stream/event create");
+        }
+        B->side.push_back(st);
+        B->join.push_back(ev);
+    }
+    // capture two LSRK4 steps of every member: ten stages return the ping-pong
+    // buffers to their starting roles, so the graph can be replayed as is
+    std::vector<int> cur0(n);
+    for (int i = 0; i < n; ++i) cur0[i] = B->members[i]->cur;
+    if ((e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        batch_release(B);
+        return cuda_fail(e, "begin capture");
+    }
+    int rc = DGM_OK;
+    cudaEventRecord(B->fork, B->stream);
+    for (int i = 0; i < n && rc == DGM_OK; ++i) {
+        cudaStreamWaitEvent(B->side[i], B->fork, 0);
+        for (int step = 0; step < 2 && rc == DGM_OK; ++step) rc = member_step(B->members[i], B->side[i]);
+        cudaEventRecord(B->join[i], B->side[i]);
+        cudaStreamWaitEvent(B->stream, B->join[i], 0);
+    }
+    e = cudaStreamEndCapture(B->stream, &B->graph);
+    for (int i = 0; i < n; ++i) B->members[i]->cur = cur0[i];
+    if (rc != DGM_OK || e != cudaSuccess) {
+        batch_release(B);
+        return rc ? fail(rc, "stage launch during capture failed") : cuda_fail(e, "end capture");
+    }
+    if ((e = cudaGraphInstantiate(&B->exec, B->graph, 0)) != cudaSuccess) {
+        batch_release(B);
+        return cuda_fail(e, "graph instantiate");
+    }
+    *out = B;
+    return DGM_OK;
+}
+
+extern "C" int dgm_batch_advance(dgm_batch* B, int64_t n_steps, const double* t0) {
+    if (!B) return fail(DGM_EINVAL, "null batch");
+    if (n_steps < 0) return fail(DGM_EINVAL, "negative step count");
+    const int n = int(B->members.size());
+    cudaError_t e;
+    // order after work queued on the caller's stream and on each member's stream
+    if ((e = cudaEventRecord(B->fork, B->user)) != cudaSuccess) return cuda_fail(e, "event record");
+    if ((e = cudaStreamWaitEvent(B->stream, B->fork, 0)) != cudaSuccess) return cuda_fail(e, "wait");
+    for (int i = 0; i < n; ++i) {
+        dgm_plan* P = B->members[i];
+        if ((e = cudaEventRecord(B->join[i], P->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+        if ((e = cudaStreamWaitEvent(B->stream, B->join[i], 0)) != cudaSuccess) return cuda_fail(e, "wait");
+        const double t = t0 ? t0[i] : 0.0;
+        if ((e = cudaMemcpyAsync(P->geom + P->off_time, &t, sizeof(double), cudaMemcpyHostToDevice,
+                                 B->stream)) != cudaSuccess)
+            return cuda_fail(e, "clock upload");
+    }
+    // the clock uploads read host memory: finish them before it goes out of scope
+    if ((e = cudaStreamSynchronize(B->stream)) != cudaSuccess) return cuda_fail(e, "clock sync");
+    for (int64_t k = 0; k + 1 < n_steps; k += 2)
+        if ((e = cudaGraphLaunch(B->exec, B->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    if (n_steps % 2) {
+        for (int i = 0; i < n; ++i) {
+            int rc = member_step(B->members[i], B->stream);
+            if (rc) return fail(rc, "stage kernel launch failed");
+        }
+    }
+    if ((e = cudaEventRecord(B->fork, B->stream)) != cudaSuccess) return cuda_fail(e, "event record");
+    for (int i = 0; i < n; ++i)
+        if ((e = cudaStreamWaitEvent(B->members[i]->stream, B->fork, 0)) != cudaSuccess)
+            return cuda_fail(e, "wait");
+    if ((e = cudaStreamWaitEvent(B->user, B->fork, 0)) != cudaSuccess) return cuda_fail(e, "wait");
+    return DGM_OK;
+}
+
+extern "C" void dgm_batch_destroy(dgm_batch* B) { batch_release(B); }
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint driver (dgm_forward_record / dgm_adjoint).
+template <typename R>
+__global__ void axpby_kernel(R* y, const R* x, double a, double b, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = (a == 0.0 ? R(0) : R(a) * y[i]) + R(b) * x[i];
+}
+
+// lu[(j N + l), e_r S + s] += sum_c W_r[c][j N + l] g[s][r][c], receivers in a fixed order
+template <typename R>
+__global__ void inject_receivers(R* lu, const double* rec, int nrec, int64_t K, int S, int N,
+                                 const double* g) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t C = K * S;
+    for (int r = 0; r < nrec; ++r) {
+        const double* w = rec + int64_t(r) * (REC_HDR + 9 * N);
+        const int64_t col = int64_t(w[0]) * S + s;
+        const double g0 = g[(int64_t(s) * nrec + r) * 3 + 0];
+        const double g1 = g[(int64_t(s) * nrec + r) * 3 + 1];
+        const double g2 = g[(int64_t(s) * nrec + r) * 3 + 2];
+        for (int jl = 0; jl < 3 * N; ++jl)
+            lu[int64_t(jl) * C + col] += R(w[REC_HDR + jl] * g0 + w[REC_HDR + 3 * N + jl] * g1 +
+                                           w[REC_HDR + 6 * N + jl] * g2);
+    }
+}
+
+__global__ void reduce_columns(const double* gcol, int64_t K, int S, double* deps, double* dmu) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= K) return;
+    const int64_t C = K * S;
+    double a = 0.0, b = 0.0;
+    for (int s = 0; s < S; ++s) {
+        a += gcol[e * S + s];
+        b += gcol[C + e * S + s];
+    }
+    deps[e] = a;
+    dmu[e] = b;
+}
+
+namespace {
+struct AdjLayout {
+    size_t fb = 0, ab = 0, sb = 0;   // field, aux, state bytes
+    int64_t seg = 0, nseg = 0;
+    size_t ck = 0, sg = 0, st = 0, tmp = 0, res = 0, lu = 0, lr = 0, raw = 0, jmp = 0, grad = 0, total = 0;
+};
+
+AdjLayout adj_layout(const dgm_plan* P, int64_t n) {
+    AdjLayout L;
+    const int rs = P->kt->real_size;
+    const int64_t C = P->mesh.K * P->opt.n_columns;
+    L.fb = align256(size_t(6) * P->N * C * rs);
+    L.ab = align256(size_t(6) * P->N * P->mesh.npml * P->opt.n_columns * rs);
+    L.sb = L.fb + L.ab;
+    L.seg = std::max<int64_t>(1, int64_t(std::ceil(std::sqrt(double(std::max<int64_t>(n, 1))))));
+    L.nseg = (n + L.seg - 1) / L.seg;
+    size_t off = 0;
+    L.ck = off; off += L.sb * size_t(std::max<int64_t>(L.nseg, 1));
+    L.sg = off; off += L.sb * size_t(L.seg + 1);
+    L.st = off; off += L.sb * 5;
+    L.tmp = off; off += L.sb * 2;
+    L.res = off; off += L.sb;
+    L.lu = off; off += L.sb;
+    L.lr = off; off += L.sb;
+    L.raw = off; off += L.fb;
+    L.jmp = off; off += align256(size_t(24) * P->NF * C * rs);
+    L.grad = off; off += align256(sizeof(double) * 2 * C);
+    L.total = off;
+    return L;
+}
+
+struct StateRef {
+    void* f;
+    void* a;
+};
+
+StateRef slot(unsigned char* ws, size_t base, size_t idx, const AdjLayout& L) {
+    unsigned char* p = ws + base + idx * L.sb;
+    return StateRef{p, L.ab ? p + L.fb : nullptr};
+}
+}  // namespace
+
+extern "C" int dgm_set_materials(dgm_plan* P, const double* eps, const double* mu) {
+    if (!P || !eps || !mu) return fail(DGM_EINVAL, "null argument");
+    const int64_t K = P->mesh.K;
+    for (int64_t e = 0; e < K; ++e)
+        if (!(eps[e] > 0.0) || !(mu[e] > 0.0) || !std::isfinite(eps[e]) || !std::isfinite(mu[e]))
+            return fail(DGM_EINVAL, "eps and mu must be positive and finite");
+    std::copy(eps, eps + K, P->mesh.geo.begin() + size_t(G_EPS) * K);
+    std::copy(mu, mu + K, P->mesh.geo.begin() + size_t(G_MU) * K);
+    if (!P->bound) return DGM_OK;
+    cudaError_t e = cudaMemcpyAsync(P->geom + P->off_geo + sizeof(double) * G_EPS * K,
+                                    P->mesh.geo.data() + size_t(G_EPS) * K, sizeof(double) * 2 * K,
+                                    cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload materials");
+    if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "materials sync");
+    return DGM_OK;
+}
+
+extern "C" int dgm_adjoint_workspace(const dgm_plan* P, int64_t n_steps, size_t* bytes) {
+    if (!P || !bytes || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
+    *bytes = adj_layout(P, n_steps).total;
+    return DGM_OK;
+}
+
+static int copy_state(dgm_plan* P, StateRef dst, const void* f, const void* a, const AdjLayout& L) {
+    cudaError_t e = cudaMemcpyAsync(dst.f, f, L.fb, cudaMemcpyDeviceToDevice, P->stream);
+    if (e == cudaSuccess && L.ab && a) e = cudaMemcpyAsync(dst.a, a, L.ab, cudaMemcpyDeviceToDevice, P->stream);
+    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "state copy");
+}
+
+extern "C" int dgm_forward_record(dgm_plan* P, int64_t n_steps, double t0, double* records, void* ws_) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (P->opt.integrator != DGM_LSRK4) return fail(DGM_EUNSUP, "the adjoint needs LSRK4");
+    if (!records || !ws_ || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
+    if (reinterpret_cast<uintptr_t>(ws_) % 256) return fail(DGM_EINVAL, "workspace must be 256-byte aligned");
+    unsigned char* ws = static_cast<unsigned char*>(ws_);
+    const AdjLayout L = adj_layout(P, n_steps);
+    const int64_t per = int64_t(P->opt.n_columns) * P->n_rec * 3;
+    for (int64_t n = 0; n < n_steps; ++n) {
+        if (n % L.seg == 0) {
+            int rc = copy_state(P, slot(ws, L.ck, size_t(n / L.seg), L), P->fields[P->cur], P->aux[P->cur], L);
+            if (rc) return rc;
+        }
+        int rc = dgm_advance(P, 1, t0 + double(n) * P->opt.dt);
+        if (rc) return rc;
+        rc = dgm_sample_receivers(P, P->fields[P->cur], records + n * per);
+        if (rc) return rc;
+    }
+    return DGM_OK;
+}
+
+// LSRK4 stages of one step from `in`; stage inputs to st[1..nst-1] (st[0] = in),
+// the step's result to `out` when nst == 5 and out.f != nullptr.
+static int lsrk_stages(dgm_plan* P, StateRef in, StateRef* st, int nst, StateRef tmp0, StateRef tmp1,
+                       StateRef res, StateRef out, double t) {
+    StageParams prm;
+    stage_params(P, prm);
+    const double dt = P->opt.dt;
+    StateRef cur = in;
+    for (int k = 0; k < 5; ++k) {
+        StateRef nxt;
+        if (k < 4) nxt = st ? st[k + 1] : ((k % 2) ? tmp1 : tmp0);
+        else nxt = out;
+        if (k >= nst && !out.f) break;
+        prm.u = cur.f;
+        prm.u_out = nxt.f;
+        prm.aux = cur.a;
+        prm.aux_out = nxt.a;
+        prm.res = res.f;
+        prm.aux_res = res.a;
+        prm.t = t + LSRK_C[k] * dt;
+        prm.a = LSRK_A[k];
+        prm.b = LSRK_B[k];
+        int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+        if (rc) return fail(rc, "stage kernel launch failed");
+        cur = nxt;
+    }
+    return DGM_OK;
+}
+
+template <typename R>
+static int axpby(dgm_plan* P, StateRef y, StateRef x, double a, double b, const AdjLayout& L) {
+    const int64_t nf = int64_t(L.fb / sizeof(R));
+    axpby_kernel<R><<<1216, 256, 0, P->stream>>>(static_cast<R*>(y.f), static_cast<const R*>(x.f), a, b, nf);
+    if (L.ab) {
+        const int64_t na = int64_t(L.ab / sizeof(R));
+        axpby_kernel<R><<<1216, 256, 0, P->stream>>>(static_cast<R*>(y.a), static_cast<const R*>(x.a), a, b, na);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "axpby launch");
+}
+
+extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double* drec, void* ws_,
+                           double* deps, double* dmu) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!drec || !ws_ || !deps || !dmu || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
+    if (reinterpret_cast<uintptr_t>(ws_) % 256) return fail(DGM_EINVAL, "workspace must be 256-byte aligned");
+    unsigned char* ws = static_cast<unsigned char*>(ws_);
+    const AdjLayout L = adj_layout(P, n_steps);
+    const bool f64 = P->kt->real_size == 8;
+    const int64_t K = P->mesh.K;
+    const int Sc = P->opt.n_columns;
+    const int64_t per = int64_t(Sc) * P->n_rec * 3;
+    const double dt = P->opt.dt;
+    StateRef lu = slot(ws, L.lu, 0, L), lr = slot(ws, L.lr, 0, L), res = slot(ws, L.res, 0, L);
+    StateRef tmp0 = slot(ws, L.tmp, 0, L), tmp1 = slot(ws, L.tmp, 1, L);
+    StateRef st[5];
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(lu.f, 0, L.sb, P->stream)) != cudaSuccess) return cuda_fail(e, "clear");
+    double* gcol = reinterpret_cast<double*>(ws + L.grad);
+    if ((e = cudaMemsetAsync(gcol, 0, sizeof(double) * 2 * K * Sc, P->stream)) != cudaSuccess)
+        return cuda_fail(e, "clear");
+    const double* recw = reinterpret_cast<const double*>(P->geom + P->off_rec);
+    for (int64_t sgi = L.nseg - 1; sgi >= 0; --sgi) {
+        const int64_t start = sgi * L.seg, end = std::min(start + L.seg, n_steps);
+        int rc = copy_state(P, slot(ws, L.sg, 0, L), slot(ws, L.ck, size_t(sgi), L).f,
+                            slot(ws, L.ck, size_t(sgi), L).a, L);
+        if (rc) return rc;
+        for (int64_t i = start; i < end - 1; ++i) {   // states x_start .. x_{end-1}
+            rc = lsrk_stages(P, slot(ws, L.sg, size_t(i - start), L), nullptr, 5, tmp0, tmp1, res,
+                             slot(ws, L.sg, size_t(i - start + 1), L), t0 + double(i) * dt);
+            if (rc) return rc;
+        }
+        for (int64_t n = end - 1; n >= start; --n) {
+            if (P->n_rec > 0) {
+                if (f64)
+                    inject_receivers<double><<<(Sc + 63) / 64, 64, 0, P->stream>>>(
+                        static_cast<double*>(lu.f), recw, P->n_rec, K, Sc, P->N, drec + n * per);
+                else
+                    inject_receivers<float><<<(Sc + 63) / 64, 64, 0, P->stream>>>(
+                        static_cast<float*>(lu.f), recw, P->n_rec, K, Sc, P->N, drec + n * per);
+            }
+            const double tn = t0 + double(n) * dt;
+            st[0] = slot(ws, L.sg, size_t(n - start), L);
+            for (int k = 1; k < 5; ++k) st[k] = slot(ws, L.st, size_t(k), L);
+            rc = lsrk_stages(P, st[0], st, 4, tmp0, tmp1, res, StateRef{nullptr, nullptr}, tn);
+            if (rc) return rc;
+            for (int k = 4; k >= 0; --k) {
+                // lr = a_{k+1} lr + b_k lu  (a_5 := 0 starts each step)
+                const double a = (k == 4) ? 0.0 : LSRK_A[k + 1];
+                rc = f64 ? axpby<double>(P, lr, lu, a, LSRK_B[k], L) : axpby<float>(P, lr, lu, a, LSRK_B[k], L);
+                if (rc) return rc;
+                StageParams prm;
+                stage_params(P, prm);
+                prm.u = st[k].f;
+                prm.aux = st[k].a;
+                prm.raw = ws + L.raw;
+                prm.jumps = ws + L.jmp;
+                prm.t = tn + LSRK_C[k] * dt;
+                rc = P->kt->launch_stage(prm, MODE_RAW, P->stream);
+                if (rc) return fail(rc, "forward kernel launch failed");
+                AdjParams ap;
+                std::memset(&ap, 0, sizeof(ap));
+                ap.lr = lr.f;
+                ap.lu = lu.f;
+                ap.lr_aux = lr.a;
+                ap.lu_aux = lu.a;
+                ap.u = st[k].f;
+                ap.aux = st[k].a;
+                ap.raw = ws + L.raw;
+                ap.jumps = ws + L.jmp;
+                ap.geo = prm.geo;
+                ap.nbr = prm.nbr;
+                ap.pml = prm.pml;
+                ap.status = prm.status;
+                ap.grad = gcol;
+                ap.K = K;
+                ap.npml = P->mesh.npml;
+                ap.S = Sc;
+                ap.upwind = prm.upwind;
+                ap.dt = dt;
+                rc = P->kt->launch_adjoint(ap, P->stream);
+                if (rc) return fail(rc, "adjoint kernel launch failed");
+            }
+        }
+    }
+    reduce_columns<<<unsigned((K + 255) / 256), 256, 0, P->stream>>>(gcol, K, Sc, deps, dmu);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "reduce launch");
+}
+

@@ -30,7 +30,7 @@ enum GeoSlot {
 // Source record per column (FP64): [elem, f0, bw, t0, 0,0,0,0, w[3N]].
 constexpr int SRC_HDR = 8;
 
-enum Mode { MODE_RHS = 0, MODE_LSRK = 1, MODE_LF_E = 2, MODE_LF_H = 3 };
+enum Mode { MODE_RHS = 0, MODE_LSRK = 1, MODE_LF_E = 2, MODE_LF_H = 3, MODE_RAW = 4 };
 
 enum StatusBits { ST_OK = 0, ST_BAD_NEIGHBOUR = 1, ST_NAN = 2, ST_TIMEOUT = 4 };
 
@@ -51,12 +51,39 @@ struct StageParams {
     int32_t S;
     int32_t upwind;
     double t, dt, a, b;   // stage time, step, LSRK coefficients a_k, b_k
+    const double* tdev;   // if set: stage time = *tdev + t (device clock of graph replays)
+    void* raw;            // MODE_RAW: right-hand side before the mass inverse [6][N][K][S]
+    void* jumps;          // MODE_RAW: physical face jumps dE, dH [4][6][NF][K][S]
+};
+
+// One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms
+// dt lr . (dF/d eps_T, dF/d mu_T) u at the stage input u (per column).
+struct AdjParams {
+    const void* lr;       // adjoint residual (fields)      [6][N][K][S]
+    void* lu;             // adjoint state (fields), updated in place
+    const void* lr_aux;   // adjoint residual (PML aux)     [6][N][P][S]
+    void* lu_aux;         // adjoint state (PML aux), updated in place
+    const void* u;        // forward stage input (fields)
+    const void* aux;      // forward stage input (PML aux)
+    const void* raw;      // forward right-hand side before the mass inverse
+    const void* jumps;    // forward physical face jumps
+    const double* geo;
+    const int32_t* nbr;
+    const int32_t* pml;
+    int32_t* status;
+    double* grad;         // [2][K*S]: per-column d/d eps, d/d mu accumulators
+    int64_t K;
+    int64_t npml;
+    int32_t S;
+    int32_t upwind;
+    double dt;
 };
 
 // Kernel translation unit entry points, one set per (order, precision).
 struct KernelTable {
     int (*launch_stage)(const StageParams&, int mode, void* stream);
     int real_size;
+    int (*launch_adjoint)(const AdjParams&, void* stream);
 };
 
 const KernelTable* kernel_table(int p, int precision);

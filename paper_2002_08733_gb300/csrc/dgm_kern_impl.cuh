@@ -10,7 +10,11 @@
 #include "dgm_internal.h"
 #include "dgmax.h"
 
+#ifdef DGM_ADJ
+#include "dgm_adjoint.cuh"
+#else
 #include "dgm_stage.cuh"
+#endif
 
 namespace dgm {
 namespace {
@@ -18,8 +22,28 @@ namespace {
 constexpr int kP = DGM_P;
 using Real = DGM_REAL;
 constexpr int kTE = sizeof(Real) == 8 ? 16 : 32;   // columns per CTA
-constexpr int kNT = 192;                            // threads per CTA
+constexpr int kNT = sizeof(Real) == 8 ? 192 : 384;  // threads per CTA
 
+#ifdef DGM_ADJ
+constexpr int kTEA = sizeof(Real) == 8 ? 16 : 32;
+constexpr int kNTA = sizeof(Real) == 8 ? 192 : 384;
+int launch_adj(const AdjParams& prm, cudaStream_t st) {
+    constexpr size_t smem = adjoint_smem_bytes<kP, Real, kTEA, kNTA>();
+    static bool configured = false;
+    auto k = adjoint_kernel<kP, Real, kTEA, kNTA>;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+            cudaSuccess)
+            return DGM_ECUDA;
+        configured = true;
+    }
+    const int64_t C = prm.K * prm.S;
+    if (C <= 0) return DGM_OK;
+    const unsigned grid = unsigned((C + kTEA - 1) / kTEA);
+    k<<<grid, kNTA, smem, st>>>(prm);
+    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+}
+#else
 int launch_mode(const StageParams& prm, cudaStream_t st) {
     constexpr size_t smem = stage_smem_bytes<kP, Real, kTE>();
     static bool configured = false;
@@ -36,12 +60,19 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     k<<<grid, kNT, smem, st>>>(prm);
     return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
 }
+#endif
 
 }  // namespace
 
+#ifdef DGM_ADJ
+int DGM_LAUNCH(const AdjParams& prm, void* stream) {
+    return launch_adj(prm, static_cast<cudaStream_t>(stream));
+}
+#else
 int DGM_LAUNCH(const StageParams& prm, void* stream) {
     return launch_mode(prm, static_cast<cudaStream_t>(stream));
 }
+#endif
 
 
 

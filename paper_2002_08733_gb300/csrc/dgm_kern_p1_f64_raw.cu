@@ -1,0 +1,6 @@
+// Fused stage kernel: degree 1, double fields, forward quantities for the adjoint.
+#define DGM_P 1
+#define DGM_REAL double
+#define DGM_MODE MODE_RAW
+#define DGM_LAUNCH launch_p1_f64_raw
+#include "dgm_kern_impl.cuh"

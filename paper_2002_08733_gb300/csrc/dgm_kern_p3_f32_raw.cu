@@ -1,0 +1,6 @@
+// Fused stage kernel: degree 3, float fields, forward quantities for the adjoint.
+#define DGM_P 3
+#define DGM_REAL float
+#define DGM_MODE MODE_RAW
+#define DGM_LAUNCH launch_p3_f32_raw
+#include "dgm_kern_impl.cuh"

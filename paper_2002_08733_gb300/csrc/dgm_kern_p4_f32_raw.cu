@@ -1,0 +1,6 @@
+// Fused stage kernel: degree 4, float fields, forward quantities for the adjoint.
+#define DGM_P 4
+#define DGM_REAL float
+#define DGM_MODE MODE_RAW
+#define DGM_LAUNCH launch_p4_f32_raw
+#include "dgm_kern_impl.cuh"

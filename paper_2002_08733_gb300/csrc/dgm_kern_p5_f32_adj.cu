@@ -1,0 +1,6 @@
+// Adjoint stage kernel: degree 5, float fields.
+#define DGM_P 5
+#define DGM_REAL float
+#define DGM_ADJ 1
+#define DGM_LAUNCH launch_p5_f32_adj
+#include "dgm_kern_impl.cuh"

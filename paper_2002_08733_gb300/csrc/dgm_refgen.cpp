@@ -14,6 +14,7 @@
 // round-off of exact zeros and are dropped.  Host copies of the full
 // matrices are emitted too, so that the library can check at plan creation
 // that the compiled operators match the matrices it builds at run time.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <string>
@@ -35,7 +36,8 @@ int main(int argc, char** argv) {
     std::fprintf(f, "// Generated by dgm_refgen.cpp at build time; do not edit.\n#pragma once\n\n");
     std::fprintf(f, "namespace dgm {\n\n");
     std::fprintf(f, "template <int P, int F> struct TraceOp;\ntemplate <int P, int F> struct LiftOp;\n");
-    std::fprintf(f, "template <int P, int A> struct DerivOp;\ntemplate <int P> struct RefNnz;\n\n");
+    std::fprintf(f, "template <int P, int A> struct DerivOp;\ntemplate <int P, int A> struct DerivTOp;\n");
+    std::fprintf(f, "template <int P> struct RefNnz;\n\n");
     for (int p = 1; p <= PMAX; ++p) {
         std::vector<double> S, Rm;
         std::string err;
@@ -72,18 +74,19 @@ int main(int argc, char** argv) {
                 std::fprintf(f, ";\n");
             }
             std::fprintf(f, "  }\n};\n");
-            std::fprintf(f, "template <> struct LiftOp<%d, %d> {\n  template <typename R>\n"
+            std::fprintf(f, "template <> struct LiftOp<%d, %d> {\n  template <typename R, int LO = 0, int HI = %d>\n"
                             "  __device__ static __forceinline__ void apply(const R* g, int stride, R* acc) {\n",
-                         p, fc);
+                         p, fc, N);
             for (int m = 0; m < NF; ++m) {
-                bool any = false;
-                for (int l = 0; l < N; ++l) any = any || rv(fc, m, l) != 0.0;
-                if (!any) continue;
-                std::fprintf(f, "    { const R x = g[%d * stride];", m);
+                int lmin = N, lmax = -1;
+                for (int l = 0; l < N; ++l)
+                    if (rv(fc, m, l) != 0.0) { lmin = std::min(lmin, l); lmax = std::max(lmax, l); }
+                if (lmax < 0) continue;
+                std::fprintf(f, "    if (LO <= %d && %d < HI) { const R x = g[%d * stride];", lmax, lmin, m);
                 for (int l = 0; l < N; ++l) {
                     double c = rv(fc, m, l);
                     if (c == 0.0) continue;
-                    std::fprintf(f, " acc[%d] += ", l);
+                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] += ", l, l, l);
                     lit(f, c);
                     std::fprintf(f, " * x;");
                 }
@@ -92,19 +95,42 @@ int main(int argc, char** argv) {
             std::fprintf(f, "  }\n};\n");
         }
         for (int a = 0; a < 3; ++a) {
-            std::fprintf(f, "template <> struct DerivOp<%d, %d> {\n  template <typename R>\n"
+            std::fprintf(f, "template <> struct DerivOp<%d, %d> {\n  template <typename R, int LO = 0, int HI = %d>\n"
                             "  __device__ static __forceinline__ void apply(const R* v, int stride, R sign, R* acc) {\n",
-                         p, a);
+                         p, a, N);
             for (int m = 0; m < N; ++m) {
-                bool any = false;
-                for (int l = 0; l < N; ++l) any = any || sv(a, l, m) != 0.0;
-                if (!any) continue;
-                std::fprintf(f, "    { const R x = sign * v[%d * stride];", m);
+                int lmin = N, lmax = -1;
+                for (int l = 0; l < N; ++l)
+                    if (sv(a, l, m) != 0.0) { lmin = std::min(lmin, l); lmax = std::max(lmax, l); }
+                if (lmax < 0) continue;
+                std::fprintf(f, "    if (LO <= %d && %d < HI) { const R x = sign * v[%d * stride];", lmax, lmin, m);
                 for (int l = 0; l < N; ++l) {
                     double c = sv(a, l, m);
                     if (c == 0.0) continue;
                     ++nnzS;
-                    std::fprintf(f, " acc[%d] += ", l);
+                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] += ", l, l, l);
+                    lit(f, c);
+                    std::fprintf(f, " * x;");
+                }
+                std::fprintf(f, " }\n");
+            }
+            std::fprintf(f, "  }\n};\n");
+        }
+        // transposed derivative (adjoint): acc[m] += sign sum_l S_a[l][m] v[l], rows m in [LO, HI)
+        for (int a = 0; a < 3; ++a) {
+            std::fprintf(f, "template <> struct DerivTOp<%d, %d> {\n  template <typename R, int LO = 0, int HI = %d>\n"
+                            "  __device__ static __forceinline__ void apply(const R* v, int stride, R sign, R* acc) {\n",
+                         p, a, N);
+            for (int l = 0; l < N; ++l) {
+                int mmin = N, mmax = -1;
+                for (int m = 0; m < N; ++m)
+                    if (sv(a, l, m) != 0.0) { mmin = std::min(mmin, m); mmax = std::max(mmax, m); }
+                if (mmax < 0) continue;
+                std::fprintf(f, "    if (LO <= %d && %d < HI) { const R x = sign * v[%d * stride];", mmax, mmin, l);
+                for (int m = 0; m < N; ++m) {
+                    double c = sv(a, l, m);
+                    if (c == 0.0) continue;
+                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] += ", m, m, m);
                     lit(f, c);
                     std::fprintf(f, " * x;");
                 }

@@ -110,11 +110,109 @@ __device__ __forceinline__ double source_time(double t, double f0, double bw, do
     return sin(twopi * f0 * tau) * exp(-tau * tau / (2.0 * s * s));
 }
 
-template <int P, typename R, int TE, int NT, int MODE>
-__global__ void __launch_bounds__(NT) stage_kernel(const StageParams prm) {
+// Face constants of face f of one element (written to fc[k * TE]): unit outward
+// normal, the neighbour's A^-T (own on a PEC face), flux coefficients, 2|F|,
+// PEC flag.  2|F| n = |det A| A^-T m_f with m_f = 2|F_hat| n_hat of the
+// reference face: (1,1,1), (-1,0,0), (0,-1,0), (0,0,-1).
+template <typename R, int TE>
+__device__ __forceinline__ void face_constants(int f, const R (&ait)[9], R det, R epsm, R mum,
+                                               bool active, const StageParams& prm, int64_t e,
+                                               R* fc) {
+    const int64_t K = prm.K;
+    const R m0 = R(f == 0 ? 1 : (f == 1 ? -1 : 0));
+    const R m1 = R(f == 0 ? 1 : (f == 2 ? -1 : 0));
+    const R m2 = R(f == 0 ? 1 : (f == 3 ? -1 : 0));
+    R vn[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) vn[r] = ait[3 * r + 0] * m0 + ait[3 * r + 1] * m1 + ait[3 * r + 2] * m2;
+    const R fs = sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) fc[(FC_N + r) * TE] = vn[r] / fs;
+    fc[FC_TWOF * TE] = fabs(det) * fs;
+    const R zm = sqrt(mum / epsm);
+    const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
+    R zp = zm;
+    if (code >= 0 && (code >> 2) < K) {
+        const int64_t ne = code >> 2;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = R(prm.geo[int64_t(G_AIT + k) * K + ne]);
+        zp = sqrt(R(prm.geo[int64_t(G_MU) * K + ne]) / R(prm.geo[int64_t(G_EPS) * K + ne]));
+        fc[FC_BND * TE] = R(0);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = ait[k];
+        fc[FC_BND * TE] = R(1);
+    }
+    if (prm.upwind) {
+        const R ym = R(1) / zm, yp = R(1) / zp;
+        fc[FC_CE * TE] = zp / (zm + zp);
+        fc[FC_BE * TE] = R(1) / (zm + zp);
+        fc[FC_CH * TE] = yp / (ym + yp);
+        fc[FC_BH * TE] = R(1) / (ym + yp);
+    } else {
+        fc[FC_CE * TE] = R(0.5);
+        fc[FC_BE * TE] = R(0);
+        fc[FC_CH * TE] = R(0.5);
+        fc[FC_BH * TE] = R(0);
+    }
+}
+
+// Right-hand side rows [LO, HI) of component `comp` (before the mass inverse):
+// volume curl of the other field plus the lift of the pulled-back fluxes.
+template <int P, typename R, int TE, int LO, int HI>
+__device__ __forceinline__ void rhs_rows(int comp, int c, const R* us, const R* trO, R sgn,
+                                         R (&acc)[nmodes(P)]) {
     constexpr int N = nmodes(P);
     constexpr int NF = nfmodes(P);
-    constexpr int NG = NT / TE;
+#pragma unroll
+    for (int l = 0; l < N; ++l) acc[l] = R(0);
+    // curl_x = d_y v_z - d_z v_y, curl_y = d_z v_x - d_x v_z, curl_z = d_x v_y - d_y v_x,
+    // of H for the E equation (+s_T) and of E for the H equation (-s_T)
+    const int j = comp % 3;
+    const int srcf = comp < 3 ? 3 : 0;
+    const R sg = comp < 3 ? sgn : -sgn;
+    const R* base = us + c;
+    switch (j) {
+        case 0:
+            DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 2) * N * TE, TE, sg, acc);
+            DerivOp<P, 2>::template apply<R, LO, HI>(base + (srcf + 1) * N * TE, TE, -sg, acc);
+            break;
+        case 1:
+            DerivOp<P, 2>::template apply<R, LO, HI>(base + (srcf + 0) * N * TE, TE, sg, acc);
+            DerivOp<P, 0>::template apply<R, LO, HI>(base + (srcf + 2) * N * TE, TE, -sg, acc);
+            break;
+        default:
+            DerivOp<P, 0>::template apply<R, LO, HI>(base + (srcf + 1) * N * TE, TE, sg, acc);
+            DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 0) * N * TE, TE, -sg, acc);
+            break;
+    }
+    LiftOp<P, 0>::template apply<R, LO, HI>(trO + ((0 * 6 + comp) * NF) * TE + c, TE, acc);
+    LiftOp<P, 1>::template apply<R, LO, HI>(trO + ((1 * 6 + comp) * NF) * TE + c, TE, acc);
+    LiftOp<P, 2>::template apply<R, LO, HI>(trO + ((2 * 6 + comp) * NF) * TE + c, TE, acc);
+    LiftOp<P, 3>::template apply<R, LO, HI>(trO + ((3 * 6 + comp) * NF) * TE + c, TE, acc);
+}
+
+template <int P, typename R, int TE, int NPART>
+__device__ __forceinline__ void rhs_part(int part, int comp, int c, const R* us, const R* trO,
+                                         R sgn, R (&acc)[nmodes(P)]) {
+    constexpr int N = nmodes(P);
+    static_assert(NPART >= 1 && NPART <= 4, "row partition");
+    switch (part) {
+        case 0: rhs_rows<P, R, TE, 0, (NPART == 1 ? N : N / NPART)>(comp, c, us, trO, sgn, acc); break;
+        case 1: rhs_rows<P, R, TE, N / NPART, (NPART == 2 ? N : 2 * N / NPART)>(comp, c, us, trO, sgn, acc); break;
+        case 2: rhs_rows<P, R, TE, 2 * N / NPART, (NPART == 3 ? N : 3 * N / NPART)>(comp, c, us, trO, sgn, acc); break;
+        default: rhs_rows<P, R, TE, 3 * N / NPART, N>(comp, c, us, trO, sgn, acc); break;
+    }
+}
+
+// Two resident CTAs per SM where the registers allow it: FP32 up to p = 3
+// (<= 85 registers at 384 threads), FP64 at 192 threads (<= 170 registers).
+template <int P, typename R, int TE, int NT, int MODE>
+__global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_kernel(const StageParams prm) {
+    constexpr int N = nmodes(P);
+    constexpr int NF = nfmodes(P);
+    constexpr int NG = NT / TE;                         // column groups working side by side
+    constexpr int NPART = NG >= 24 ? 4 : (NG >= 12 ? 2 : 1);  // row parts of phases 4 and 5
     constexpr bool DO_E = (MODE != MODE_LF_H);   // E equation updated
     constexpr bool DO_H = (MODE != MODE_LF_E);   // H equation updated
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -135,224 +233,228 @@ __global__ void __launch_bounds__(NT) stage_kernel(const StageParams prm) {
     const int s = active ? int(col - e * S) : 0;
     const R* u = static_cast<const R*>(prm.u);   // may alias u_out (leapfrog)
 
-    // ---- phase 1: tile coefficients and element constants -------------------
-    for (int r = grp; r < 6 * N; r += NG) us[r * TE + c] = active ? u[int64_t(r) * C + col] : R(0);
+    // ---- phase 1: tile coefficients, element and face constants --------------
+    // groups 0..3 compute the face constants of face f = group straight from
+    // global memory while the other groups stage the tile's coefficients
+    constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
+    if (grp < FACE_GROUPS) {
+        const int f = grp;
+        R ait[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ait[k] = active ? R(prm.geo[int64_t(G_AIT + k) * K + e]) : R(k % 4 == 0);
+        const R det = active ? R(prm.geo[int64_t(G_DET) * K + e]) : R(1);
+        const R epsm = active ? R(prm.geo[int64_t(G_EPS) * K + e]) : R(1);
+        const R mum = active ? R(prm.geo[int64_t(G_MU) * K + e]) : R(1);
+        face_constants<R, TE>(f, ait, det, epsm, mum, active, prm, e, fg + f * FG * TE + c);
+    }
+    for (int r = grp - FACE_GROUPS; r < 6 * N; r += NG - FACE_GROUPS)
+        if (r >= 0) us[r * TE + c] = active ? u[int64_t(r) * C + col] : R(0);
     for (int k = grp; k < EG; k += NG)
         eg[k * TE + c] = active ? R(prm.geo[int64_t(k) * K + e]) : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
+    if (FACE_GROUPS == 0) {
+        for (int f = grp; f < 4; f += NG) {
+            R ait[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) ait[k] = active ? R(prm.geo[int64_t(G_AIT + k) * K + e]) : R(k % 4 == 0);
+            const R det = active ? R(prm.geo[int64_t(G_DET) * K + e]) : R(1);
+            const R epsm = active ? R(prm.geo[int64_t(G_EPS) * K + e]) : R(1);
+            const R mum = active ? R(prm.geo[int64_t(G_MU) * K + e]) : R(1);
+            face_constants<R, TE>(f, ait, det, epsm, mum, active, prm, e, fg + f * FG * TE + c);
+        }
+    }
     __syncthreads();
 
-    // ---- phase 2: traces and face constants ---------------------------------
-    // items 0..23: own traces (f, comp); 24..47: neighbour traces; 48..51: face constants
-    for (int it = grp; it < 52; it += NG) {
-        if (it < 48) {
-            const int side = it / 24;
-            const int f = (it / 6) % 4;
-            const int comp = it % 6;
-            // a leapfrog half step only needs the traces of the other field
-            if (MODE == MODE_LF_E && comp < 3) continue;
-            if (MODE == MODE_LF_H && comp >= 3) continue;
-            R v[N];
-            R acc[NF];
-            R* dst = (side == 0 ? trO : trN) + ((f * 6 + comp) * NF) * TE + c;
-            if (side == 0) {
+    // ---- phase 2: traces ------------------------------------------------------
+    // Own traces: item (component, pair of faces) shares one load of the
+    // component's coefficients between two faces.  Neighbour traces: item
+    // (face, component); the neighbour's coefficients are requested before the
+    // own-trace arithmetic so that their latency overlaps it.
+    {
+        constexpr int NOWN = 12, NNBR = 24;
+        constexpr int ROUNDS = (NNBR + NG - 1) / NG;
+#pragma unroll 1
+        for (int rr = 0; rr < ROUNDS; ++rr) {
+            const int ni = grp + rr * NG;           // neighbour item
+            const int oi = ni;                      // own item handled in the same round
+            // neighbour item: face f, component comp
+            bool do_nbr = ni < NNBR;
+            const int nf = ni / 6, ncomp = ni % 6;
+            if (MODE == MODE_LF_E && ncomp < 3) do_nbr = false;
+            if (MODE == MODE_LF_H && ncomp >= 3) do_nbr = false;
+            int32_t code = -1;
+            if (do_nbr && active) code = prm.nbr[int64_t(nf) * K + e];
+            const int64_t ne = code >> 2;
+            const bool has_nbr = do_nbr && code >= 0 && ne < K;
+            if (do_nbr && code >= 0 && ne >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
+            R vn[N];
+            if (has_nbr) {
+                const int64_t ncol = ne * S + s;
 #pragma unroll
-                for (int l = 0; l < N; ++l) v[l] = us[(comp * N + l) * TE + c];
-                trace_any<P, R>(f, v, acc);
-            } else {
-                const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
-                if (code < 0) {
+                for (int l = 0; l < N; ++l) vn[l] = u[int64_t(ncomp * N + l) * C + ncol];
+            }
+            // own item: component ocomp, faces 2*fp and 2*fp+1
+            if (oi < NOWN) {
+                const int ocomp = oi % 6, fp = oi / 6;
+                bool do_own = true;
+                if (MODE == MODE_LF_E && ocomp < 3) do_own = false;
+                if (MODE == MODE_LF_H && ocomp >= 3) do_own = false;
+                if (do_own) {
+                    R v[N];
+                    R acc[NF];
 #pragma unroll
-                    for (int m = 0; m < NF; ++m) acc[m] = R(0);
-                } else {
-                    const int64_t ne = code >> 2;
-                    const int fp = code & 3;
-                    const int64_t ncol = ne * S + s;
-                    if (ne >= K) {
-                        atomicOr(prm.status, ST_BAD_NEIGHBOUR);
+                    for (int l = 0; l < N; ++l) v[l] = us[(ocomp * N + l) * TE + c];
 #pragma unroll
-                        for (int m = 0; m < NF; ++m) acc[m] = R(0);
-                    } else {
+                    for (int h = 0; h < 2; ++h) {
+                        const int f = 2 * fp + h;
+                        trace_any<P, R>(f, v, acc);
+                        R* dst = trO + ((f * 6 + ocomp) * NF) * TE + c;
 #pragma unroll
-                        for (int l = 0; l < N; ++l) v[l] = u[int64_t(comp * N + l) * C + ncol];
-                        trace_any<P, R>(fp, v, acc);
+                        for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
                     }
                 }
             }
+            if (do_nbr) {
+                R acc[NF];
+                if (has_nbr) {
+                    trace_any<P, R>(code & 3, vn, acc);
+                } else {
 #pragma unroll
-            for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
-        } else {
-            const int f = it - 48;
-            R ait[9];
+                    for (int m = 0; m < NF; ++m) acc[m] = R(0);
+                }
+                R* dst = trN + ((nf * 6 + ncomp) * NF) * TE + c;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
-            const R det = eg[G_DET * TE + c];
-            // 2|F_hat| n_hat of reference face f: (1,1,1), (-1,0,0), (0,-1,0), (0,0,-1)
-            R mref[3] = {R(f == 0 ? 1 : (f == 1 ? -1 : 0)), R(f == 0 ? 1 : (f == 2 ? -1 : 0)),
-                         R(f == 0 ? 1 : (f == 3 ? -1 : 0))};
-            R vn[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-                vn[r] = ait[3 * r + 0] * mref[0] + ait[3 * r + 1] * mref[1] + ait[3 * r + 2] * mref[2];
-            const R fs = sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
-            R* d = fg + f * FG * TE + c;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) d[(FC_N + r) * TE] = vn[r] / fs;
-            d[FC_TWOF * TE] = fabs(det) * fs;
-            const R epsm = eg[G_EPS * TE + c], mum = eg[G_MU * TE + c];
-            const R zm = sqrt(mum / epsm);
-            const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
-            R zp = zm;
-            if (code >= 0 && (code >> 2) < K) {
-                const int64_t ne = code >> 2;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) d[(FC_AITN + k) * TE] = R(prm.geo[int64_t(G_AIT + k) * K + ne]);
-                zp = sqrt(R(prm.geo[int64_t(G_MU) * K + ne]) / R(prm.geo[int64_t(G_EPS) * K + ne]));
-                d[FC_BND * TE] = R(0);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) d[(FC_AITN + k) * TE] = ait[k];
-                d[FC_BND * TE] = R(1);
-            }
-            if (prm.upwind) {
-                const R ym = R(1) / zm, yp = R(1) / zp;
-                d[FC_CE * TE] = zp / (zm + zp);
-                d[FC_BE * TE] = R(1) / (zm + zp);
-                d[FC_CH * TE] = yp / (ym + yp);
-                d[FC_BH * TE] = R(1) / (ym + yp);
-            } else {
-                d[FC_CE * TE] = R(0.5);
-                d[FC_BE * TE] = R(0);
-                d[FC_CH * TE] = R(0.5);
-                d[FC_BH * TE] = R(0);
+                for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
             }
         }
     }
     __syncthreads();
 
-    // ---- phase 3: numerical flux per (face, face mode) ----------------------
-    for (int it = grp; it < 4 * NF; it += NG) {
-        const int f = it / NF;
-        const int m = it % NF;
-        const R* d = fg + f * FG * TE + c;
-        R ait[9], aitn[9], n[3];
+    // ---- phase 3: numerical flux per (face, chunk of face modes) -------------
+    {
+        constexpr int CHUNKS = NG >= 12 ? (NG / 4) : 1;      // face-mode chunks per face
+        for (int it = grp; it < 4 * CHUNKS; it += NG) {
+            const int f = it / CHUNKS;
+            const int ch = it % CHUNKS;
+            const R* d = fg + f * FG * TE + c;
+            R ait[9], aitn[9], n[3];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            ait[k] = eg[(G_AIT + k) * TE + c];
-            aitn[k] = d[(FC_AITN + k) * TE];
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r) n[r] = d[(FC_N + r) * TE];
-        const bool bnd = d[FC_BND * TE] != R(0);
-        R* own = trO + (f * 6 * NF + m) * TE + c;
-        const R* nbt = trN + (f * 6 * NF + m) * TE + c;
-        R dE[3] = {0, 0, 0}, dH[3] = {0, 0, 0};
-        // physical traces X = A^-T x_ref on each side
-        if (DO_H || MODE == MODE_RHS || MODE == MODE_LSRK) {   // E traces needed by flux_H and upwind flux_E
-            R em[3], ep[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                em[r] = R(0);
-                ep[r] = R(0);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    em[r] += ait[3 * r + k] * own[k * NF * TE];
-                    ep[r] += aitn[3 * r + k] * nbt[k * NF * TE];
-                }
+            for (int k = 0; k < 9; ++k) {
+                ait[k] = eg[(G_AIT + k) * TE + c];
+                aitn[k] = d[(FC_AITN + k) * TE];
             }
 #pragma unroll
-            for (int r = 0; r < 3; ++r) dE[r] = bnd ? R(-2) * em[r] : ep[r] - em[r];
-        }
-        if (DO_E) {
-            R hm[3], hp[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                hm[r] = R(0);
-                hp[r] = R(0);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    hm[r] += ait[3 * r + k] * own[(3 + k) * NF * TE];
-                    hp[r] += aitn[3 * r + k] * nbt[(3 + k) * NF * TE];
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < 3; ++r) dH[r] = bnd ? R(0) : hp[r] - hm[r];
-        }
-        const R twoF = d[FC_TWOF * TE];
-        R nxdE[3], nxdH[3], nnxdE[3], nnxdH[3];
-        cross3(n, dE, nxdE);
-        cross3(n, dH, nxdH);
-        cross3(n, nxdE, nnxdE);
-        cross3(n, nxdH, nnxdH);
-        if (DO_E) {
+            for (int r = 0; r < 3; ++r) n[r] = d[(FC_N + r) * TE];
+            const bool bnd = d[FC_BND * TE] != R(0);
+            const R twoF = d[FC_TWOF * TE];
             const R ce = d[FC_CE * TE], be = d[FC_BE * TE];
-            R fl[3];
+            const R chc = d[FC_CH * TE], bh = d[FC_BH * TE];
+            const int m0 = ch * NF / CHUNKS, m1 = (ch + 1) * NF / CHUNKS;
+            for (int m = m0; m < m1; ++m) {
+                R* own = trO + (f * 6 * NF + m) * TE + c;
+                const R* nbt = trN + (f * 6 * NF + m) * TE + c;
+                R dE[3] = {0, 0, 0}, dH[3] = {0, 0, 0};
+                // physical traces X = A^-T x_ref on each side
+                if (MODE != MODE_LF_E) {   // E traces: flux_H and the upwind part of flux_E
+                    R tm[3], tp[3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) fl[r] = ce * nxdH[r] - be * nnxdE[r];
-            // g = 2|F| A^-1 flux, A^-1 = (A^-T)^T
+                    for (int k = 0; k < 3; ++k) {
+                        tm[k] = own[k * NF * TE];
+                        tp[k] = nbt[k * NF * TE];
+                    }
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
-                own[j * NF * TE] = twoF * (ait[j] * fl[0] + ait[3 + j] * fl[1] + ait[6 + j] * fl[2]);
-        }
-        if (DO_H) {
-            const R ch = d[FC_CH * TE], bh = d[FC_BH * TE];
-            R fl[3];
+                    for (int r = 0; r < 3; ++r) {
+                        const R em = ait[3 * r] * tm[0] + ait[3 * r + 1] * tm[1] + ait[3 * r + 2] * tm[2];
+                        const R ep = aitn[3 * r] * tp[0] + aitn[3 * r + 1] * tp[1] + aitn[3 * r + 2] * tp[2];
+                        dE[r] = bnd ? R(-2) * em : ep - em;
+                    }
+                }
+                if (DO_E) {
+                    R tm[3], tp[3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) fl[r] = ch * nxdE[r] + bh * nnxdH[r];
+                    for (int k = 0; k < 3; ++k) {
+                        tm[k] = own[(3 + k) * NF * TE];
+                        tp[k] = nbt[(3 + k) * NF * TE];
+                    }
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
-                own[(3 + j) * NF * TE] = -twoF * (ait[j] * fl[0] + ait[3 + j] * fl[1] + ait[6 + j] * fl[2]);
+                    for (int r = 0; r < 3; ++r) {
+                        const R hm = ait[3 * r] * tm[0] + ait[3 * r + 1] * tm[1] + ait[3 * r + 2] * tm[2];
+                        const R hp = aitn[3 * r] * tp[0] + aitn[3 * r + 1] * tp[1] + aitn[3 * r + 2] * tp[2];
+                        dH[r] = bnd ? R(0) : hp - hm;
+                    }
+                }
+                if (MODE == MODE_RAW && active) {
+                    R* jp = static_cast<R*>(prm.jumps);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        jp[int64_t((f * 6 + r) * NF + m) * C + col] = dE[r];
+                        jp[int64_t((f * 6 + 3 + r) * NF + m) * C + col] = dH[r];
+                    }
+                }
+                R nxdE[3], nxdH[3], nnxdE[3], nnxdH[3];
+                cross3(n, dE, nxdE);
+                cross3(n, dH, nxdH);
+                cross3(n, nxdE, nnxdE);
+                cross3(n, nxdH, nnxdH);
+                if (DO_E) {
+                    R fl[3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) fl[r] = ce * nxdH[r] - be * nnxdE[r];
+                    // g = 2|F| A^-1 flux, A^-1 = (A^-T)^T
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        own[j * NF * TE] = twoF * (ait[j] * fl[0] + ait[3 + j] * fl[1] + ait[6 + j] * fl[2]);
+                }
+                if (DO_H) {
+                    R fl[3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) fl[r] = chc * nxdE[r] + bh * nnxdH[r];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        own[(3 + j) * NF * TE] = -twoF * (ait[j] * fl[0] + ait[3 + j] * fl[1] + ait[6 + j] * fl[2]);
+                }
+            }
         }
     }
     __syncthreads();
 
-    // ---- phase 4: volume curl + lift per component ---------------------------
+    // ---- phase 4: volume curl + lift per (component, row part) -----------------
     R* rh = trN;   // [6][N][TE], the neighbour traces are dead now
-    for (int comp = grp; comp < 6; comp += NG) {
+    for (int it = grp; it < 6 * NPART; it += NG) {
+        const int comp = it / NPART;
+        const int part = it % NPART;
         if (!DO_E && comp < 3) continue;
         if (!DO_H && comp >= 3) continue;
-        R acc[N];
-#pragma unroll
-        for (int l = 0; l < N; ++l) acc[l] = R(0);
         const R sgn = eg[G_DET * TE + c] < R(0) ? R(-1) : R(1);
-        // curl_x = d_y v_z - d_z v_y, curl_y = d_z v_x - d_x v_z, curl_z = d_x v_y - d_y v_x,
-        // applied to H for the E equation (+s) and to E for the H equation (-s)
-        const int j = comp % 3;
-        const int srcf = comp < 3 ? 3 : 0;
-        const R sg = comp < 3 ? sgn : -sgn;
-        const R* base = us + c;
-        switch (j) {
-            case 0:
-                deriv_acc<P, R, 1>(base + (srcf + 2) * N * TE, TE, sg, acc);
-                deriv_acc<P, R, 2>(base + (srcf + 1) * N * TE, TE, -sg, acc);
-                break;
-            case 1:
-                deriv_acc<P, R, 2>(base + (srcf + 0) * N * TE, TE, sg, acc);
-                deriv_acc<P, R, 0>(base + (srcf + 2) * N * TE, TE, -sg, acc);
-                break;
-            default:
-                deriv_acc<P, R, 0>(base + (srcf + 1) * N * TE, TE, sg, acc);
-                deriv_acc<P, R, 1>(base + (srcf + 0) * N * TE, TE, -sg, acc);
-                break;
-        }
-        lift_face<P, R, 0>(trO + ((0 * 6 + comp) * NF) * TE + c, TE, acc);
-        lift_face<P, R, 1>(trO + ((1 * 6 + comp) * NF) * TE + c, TE, acc);
-        lift_face<P, R, 2>(trO + ((2 * 6 + comp) * NF) * TE + c, TE, acc);
-        lift_face<P, R, 3>(trO + ((3 * 6 + comp) * NF) * TE + c, TE, acc);
+        R acc[N];
+        rhs_part<P, R, TE, NPART>(part, comp, c, us, trO, sgn, acc);
+        const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
         if (comp < 3 && prm.src != nullptr && active) {
             const double* rec = prm.src + int64_t(s) * (SRC_HDR + 3 * N);
             if (int64_t(rec[0]) == e) {
-                const R g = R(source_time(prm.t, rec[1], rec[2], rec[3]));
+                const double tt = prm.tdev ? *prm.tdev + prm.t : prm.t;
+                const R g = R(source_time(tt, rec[1], rec[2], rec[3]));
 #pragma unroll
-                for (int l = 0; l < N; ++l) acc[l] -= g * R(rec[SRC_HDR + j * N + l]);
+                for (int l = 0; l < N; ++l)
+                    if (l >= lo && l < hi) acc[l] -= g * R(rec[SRC_HDR + (comp % 3) * N + l]);
             }
         }
 #pragma unroll
-        for (int l = 0; l < N; ++l) rh[(comp * N + l) * TE + c] = acc[l];
+        for (int l = 0; l < N; ++l)
+            if (l >= lo && l < hi) rh[(comp * N + l) * TE + c] = acc[l];
+        if (MODE == MODE_RAW && active) {
+            R* rw = static_cast<R*>(prm.raw);
+#pragma unroll
+            for (int l = 0; l < N; ++l)
+                if (l >= lo && l < hi) rw[int64_t(comp * N + l) * C + col] = acc[l];
+        }
     }
+    if (MODE == MODE_RAW) return;   // forward quantities for the adjoint only
     __syncthreads();
 
     // ---- phase 5: mass-block inverse, PML, update ------------------------------
-    for (int comp = grp; comp < 6; comp += NG) {
+    for (int it = grp; it < 6 * NPART; it += NG) {
+        const int comp = it / NPART;
+        const int part = it % NPART;
         if (!DO_E && comp < 3) continue;
         if (!DO_H && comp >= 3) continue;
         if (!active) continue;
@@ -378,11 +480,16 @@ __global__ void __launch_bounds__(NT) stage_kernel(const StageParams prm) {
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b) AT[a][b] *= det;
+        // row j of A^T, selected without dynamic indexing (keeps AT in registers)
+        R atj[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) atj[b] = j == 0 ? AT[0][b] : (j == 1 ? AT[1][b] : AT[2][b]);
+        // row j of the 3x3 mass-block inverse A^T A / (mat |det|)
         R brow[3];
         const R inv = R(1) / (mat * fabs(det));
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            brow[k] = inv * (AT[j][0] * AT[k][0] + AT[j][1] * AT[k][1] + AT[j][2] * AT[k][2]);
+            brow[k] = inv * (atj[0] * AT[k][0] + atj[1] * AT[k][1] + atj[2] * AT[k][2]);
         // PML rows: (A^T D A^-T)[j][k] = sum_a A^T[j][a] D_a A^-T[a][k]
         int32_t pi = -1;
         if (prm.pml != nullptr) pi = prm.pml[e];
@@ -397,7 +504,7 @@ __global__ void __launch_bounds__(NT) stage_kernel(const StageParams prm) {
             for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const R w = AT[j][a] * ait[3 * a + k];
+                    const R w = atj[a] * ait[3 * a + k];
                     eta_row[k] += w * et3[a];
                     sig_row[k] += w * sg3[a];
                     xi_row[k] += w * xi3[a];
@@ -411,8 +518,9 @@ __global__ void __launch_bounds__(NT) stage_kernel(const StageParams prm) {
         R* __restrict__ auxo = static_cast<R*>(prm.aux_out);
         R* __restrict__ auxr = static_cast<R*>(prm.aux_res);
         const R dt = R(prm.dt), ca = R(prm.a), cb = R(prm.b);
-#pragma unroll 4
-        for (int l = 0; l < N; ++l) {
+        const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
+#pragma unroll 2
+        for (int l = lo; l < hi; ++l) {
             const R r0 = rh[((fb + 0) * N + l) * TE + c];
             const R r1 = rh[((fb + 1) * N + l) * TE + c];
             const R r2 = rh[((fb + 2) * N + l) * TE + c];

@@ -8,38 +8,56 @@ int launch_p1_f32_rhs(const StageParams&, void*);
 int launch_p1_f32_lsrk(const StageParams&, void*);
 int launch_p1_f32_lfe(const StageParams&, void*);
 int launch_p1_f32_lfh(const StageParams&, void*);
+int launch_p1_f32_raw(const StageParams&, void*);
+int launch_p1_f32_adj(const AdjParams&, void*);
 int launch_p1_f64_rhs(const StageParams&, void*);
 int launch_p1_f64_lsrk(const StageParams&, void*);
 int launch_p1_f64_lfe(const StageParams&, void*);
 int launch_p1_f64_lfh(const StageParams&, void*);
+int launch_p1_f64_raw(const StageParams&, void*);
+int launch_p1_f64_adj(const AdjParams&, void*);
 int launch_p2_f32_rhs(const StageParams&, void*);
 int launch_p2_f32_lsrk(const StageParams&, void*);
 int launch_p2_f32_lfe(const StageParams&, void*);
 int launch_p2_f32_lfh(const StageParams&, void*);
+int launch_p2_f32_raw(const StageParams&, void*);
+int launch_p2_f32_adj(const AdjParams&, void*);
 int launch_p2_f64_rhs(const StageParams&, void*);
 int launch_p2_f64_lsrk(const StageParams&, void*);
 int launch_p2_f64_lfe(const StageParams&, void*);
 int launch_p2_f64_lfh(const StageParams&, void*);
+int launch_p2_f64_raw(const StageParams&, void*);
+int launch_p2_f64_adj(const AdjParams&, void*);
 int launch_p3_f32_rhs(const StageParams&, void*);
 int launch_p3_f32_lsrk(const StageParams&, void*);
 int launch_p3_f32_lfe(const StageParams&, void*);
 int launch_p3_f32_lfh(const StageParams&, void*);
+int launch_p3_f32_raw(const StageParams&, void*);
+int launch_p3_f32_adj(const AdjParams&, void*);
 int launch_p3_f64_rhs(const StageParams&, void*);
 int launch_p3_f64_lsrk(const StageParams&, void*);
 int launch_p3_f64_lfe(const StageParams&, void*);
 int launch_p3_f64_lfh(const StageParams&, void*);
+int launch_p3_f64_raw(const StageParams&, void*);
+int launch_p3_f64_adj(const AdjParams&, void*);
 int launch_p4_f32_rhs(const StageParams&, void*);
 int launch_p4_f32_lsrk(const StageParams&, void*);
 int launch_p4_f32_lfe(const StageParams&, void*);
 int launch_p4_f32_lfh(const StageParams&, void*);
+int launch_p4_f32_raw(const StageParams&, void*);
+int launch_p4_f32_adj(const AdjParams&, void*);
 int launch_p4_f64_rhs(const StageParams&, void*);
 int launch_p4_f64_lsrk(const StageParams&, void*);
 int launch_p4_f64_lfe(const StageParams&, void*);
 int launch_p4_f64_lfh(const StageParams&, void*);
+int launch_p4_f64_raw(const StageParams&, void*);
+int launch_p4_f64_adj(const AdjParams&, void*);
 int launch_p5_f32_rhs(const StageParams&, void*);
 int launch_p5_f32_lsrk(const StageParams&, void*);
 int launch_p5_f32_lfe(const StageParams&, void*);
 int launch_p5_f32_lfh(const StageParams&, void*);
+int launch_p5_f32_raw(const StageParams&, void*);
+int launch_p5_f32_adj(const AdjParams&, void*);
 
 namespace {
 
@@ -49,6 +67,7 @@ int launch_p1_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p1_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p1_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p1_f32_lfh(prm, st);
+        case MODE_RAW: return launch_p1_f32_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -59,6 +78,7 @@ int launch_p1_f64(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p1_f64_lsrk(prm, st);
         case MODE_LF_E: return launch_p1_f64_lfe(prm, st);
         case MODE_LF_H: return launch_p1_f64_lfh(prm, st);
+        case MODE_RAW: return launch_p1_f64_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -69,6 +89,7 @@ int launch_p2_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p2_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p2_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p2_f32_lfh(prm, st);
+        case MODE_RAW: return launch_p2_f32_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -79,6 +100,7 @@ int launch_p2_f64(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p2_f64_lsrk(prm, st);
         case MODE_LF_E: return launch_p2_f64_lfe(prm, st);
         case MODE_LF_H: return launch_p2_f64_lfh(prm, st);
+        case MODE_RAW: return launch_p2_f64_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -89,6 +111,7 @@ int launch_p3_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p3_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p3_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p3_f32_lfh(prm, st);
+        case MODE_RAW: return launch_p3_f32_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -99,6 +122,7 @@ int launch_p3_f64(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p3_f64_lsrk(prm, st);
         case MODE_LF_E: return launch_p3_f64_lfe(prm, st);
         case MODE_LF_H: return launch_p3_f64_lfh(prm, st);
+        case MODE_RAW: return launch_p3_f64_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -109,6 +133,7 @@ int launch_p4_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p4_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p4_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p4_f32_lfh(prm, st);
+        case MODE_RAW: return launch_p4_f32_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -119,6 +144,7 @@ int launch_p4_f64(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p4_f64_lsrk(prm, st);
         case MODE_LF_E: return launch_p4_f64_lfe(prm, st);
         case MODE_LF_H: return launch_p4_f64_lfh(prm, st);
+        case MODE_RAW: return launch_p4_f64_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
@@ -129,20 +155,21 @@ int launch_p5_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK: return launch_p5_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p5_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p5_f32_lfh(prm, st);
+        case MODE_RAW: return launch_p5_f32_raw(prm, st);
         default: return DGM_EINVAL;
     }
 }
 
 }  // namespace
 
-extern const KernelTable kernels_p1_f32 = {launch_p1_f32, 4};
-extern const KernelTable kernels_p1_f64 = {launch_p1_f64, 8};
-extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4};
-extern const KernelTable kernels_p2_f64 = {launch_p2_f64, 8};
-extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4};
-extern const KernelTable kernels_p3_f64 = {launch_p3_f64, 8};
-extern const KernelTable kernels_p4_f32 = {launch_p4_f32, 4};
-extern const KernelTable kernels_p4_f64 = {launch_p4_f64, 8};
-extern const KernelTable kernels_p5_f32 = {launch_p5_f32, 4};
+extern const KernelTable kernels_p1_f32 = {launch_p1_f32, 4, launch_p1_f32_adj};
+extern const KernelTable kernels_p1_f64 = {launch_p1_f64, 8, launch_p1_f64_adj};
+extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4, launch_p2_f32_adj};
+extern const KernelTable kernels_p2_f64 = {launch_p2_f64, 8, launch_p2_f64_adj};
+extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4, launch_p3_f32_adj};
+extern const KernelTable kernels_p3_f64 = {launch_p3_f64, 8, launch_p3_f64_adj};
+extern const KernelTable kernels_p4_f32 = {launch_p4_f32, 4, launch_p4_f32_adj};
+extern const KernelTable kernels_p4_f64 = {launch_p4_f64, 8, launch_p4_f64_adj};
+extern const KernelTable kernels_p5_f32 = {launch_p5_f32, 4, launch_p5_f32_adj};
 
 }  // namespace dgm

@@ -32,7 +32,7 @@ class DgmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("precision", ctypes.c_int32), ("flux", ctypes.c_int32),
                 ("integrator", ctypes.c_int32), ("n_columns", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("dt", ctypes.c_double)]
+                ("max_receivers", ctypes.c_int32), ("dt", ctypes.c_double)]
 
 
 class Pml(ctypes.Structure):
@@ -58,6 +58,8 @@ _SIGS = {
     "dgm_plan_info": [_P, ctypes.POINTER(Info)],
     "dgm_bind": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
     "dgm_set_sources": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
+    "dgm_set_receivers": [_P, ctypes.c_int32, _P],
+    "dgm_sample_receivers": [_P, _P, _P],
     "dgm_rhs": [_P, _P, _P, _P, _P, ctypes.c_double],
     "dgm_leapfrog_start": [_P, ctypes.c_double],
     "dgm_advance": [_P, ctypes.c_int64, ctypes.c_double],
@@ -69,6 +71,13 @@ _SIGS = {
     "dgm_quad_points": [_P, _P],
     "dgm_project": [_P, _P, ctypes.c_int32, _P],
     "dgm_status_check": [_P],
+    "dgm_set_materials": [_P, _P, _P],
+    "dgm_adjoint_workspace": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
+    "dgm_forward_record": [_P, ctypes.c_int64, ctypes.c_double, _P, _P],
+    "dgm_adjoint": [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
+    "dgm_batch_create": [ctypes.POINTER(_P), _P, ctypes.c_int32, _P],
+    "dgm_batch_advance": [_P, ctypes.c_int64, _P],
+    "dgm_batch_destroy": [_P],
     "dgm_last_error": [],
     "dgm_plan_destroy": [_P],
 }
@@ -88,6 +97,7 @@ def load_library(path=LIB_PATH):
         fn.restype = ctypes.c_int
     lib.dgm_last_error.restype = ctypes.c_char_p
     lib.dgm_plan_destroy.restype = None
+    lib.dgm_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -109,7 +119,7 @@ class Plan:
     """Host-side plan (mesh setup, reference matrices); no GPU needed."""
 
     def __init__(self, xyz, tets, eps, mu, p, precision="fp64", flux="upwind",
-                 integrator="lsrk4", dt=1e-3, S=1, pml=None):
+                 integrator="lsrk4", dt=1e-3, S=1, pml=None, max_receivers=0):
         lib = load_library()
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         tets = np.ascontiguousarray(tets, dtype=np.int64)
@@ -119,7 +129,7 @@ class Plan:
         opt = Options(p=p, precision={"fp64": FP64, "fp32": FP32}[precision],
                       flux={"central": CENTRAL, "upwind": UPWIND}[flux],
                       integrator={"leapfrog": LEAPFROG, "lsrk4": LSRK4}[integrator],
-                      n_columns=S, dt=dt)
+                      n_columns=S, max_receivers=max_receivers, dt=dt)
         pm = None
         if pml is not None:
             pm = Pml()
@@ -282,5 +292,106 @@ class Solver(Plan):
         _check(_lib.dgm_set_sources(self.handle, len(cols), c.ctypes.data,
                                     *[a.ctypes.data for a in arr]))
 
+    def set_receivers(self, pos):
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        self.n_rec = len(pos)
+        _check(_lib.dgm_set_receivers(self.handle, len(pos), pos.ctypes.data))
+
+    def sample_receivers(self, out=None, fields=None):
+        """E at the receivers for every column -> device tensor [S, R, 3] (float64)."""
+        f = self.fields[self.current()] if fields is None else fields
+        if out is None:
+            out = self.torch.empty((self.S, self.n_rec, 3), dtype=self.torch.float64,
+                                   device=self.device)
+        _check(_lib.dgm_sample_receivers(self.handle, _ptr(f), _ptr(out)))
+        return out
+
+    def set_materials(self, eps, mu):
+        eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (self.K,)))
+        mu = np.ascontiguousarray(np.broadcast_to(np.asarray(mu, np.float64), (self.K,)))
+        _check(_lib.dgm_set_materials(self.handle, eps.ctypes.data, mu.ctypes.data))
+
+    def adjoint_workspace(self, n_steps):
+        """Caller-owned device workspace for forward_record / adjoint (256-byte aligned view)."""
+        nb = ctypes.c_size_t()
+        _check(_lib.dgm_adjoint_workspace(self.handle, int(n_steps), ctypes.byref(nb)))
+        buf = self.torch.empty(nb.value + 256, dtype=self.torch.uint8, device=self.device)
+        off = (-buf.data_ptr()) % 256
+        return buf[off:off + nb.value]
+
+    def forward_record(self, n_steps, t0, workspace):
+        """Advance n_steps recording E at the receivers -> device tensor [n, S, R, 3]."""
+        rec = self.torch.empty((n_steps, self.S, self.n_rec, 3), dtype=self.torch.float64,
+                               device=self.device)
+        _check(_lib.dgm_forward_record(self.handle, int(n_steps), float(t0), _ptr(rec),
+                                       _ptr(workspace)))
+        return rec
+
+    def adjoint(self, n_steps, t0, drecords, workspace):
+        """dL/deps, dL/dmu (device float64 [K]) from dL/drecords [n, S, R, 3]."""
+        d = drecords.to(device=self.device, dtype=self.torch.float64).contiguous()
+        deps = self.torch.empty(self.K, dtype=self.torch.float64, device=self.device)
+        dmu = self.torch.empty_like(deps)
+        _check(_lib.dgm_adjoint(self.handle, int(n_steps), float(t0), _ptr(d), _ptr(workspace),
+                                _ptr(deps), _ptr(dmu)))
+        self.torch.cuda.synchronize(self.device)
+        return deps, dmu
+
     def status(self):
         _check(_lib.dgm_status_check(self.handle))
+
+
+class Batch:
+    """Several bound LSRK4 solvers advanced together by one graph launch per two steps."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        self.stream = stream or torch.cuda.current_stream()
+        arr = (_P * len(self.solvers))(*[s.handle for s in self.solvers])
+        h = _P()
+        _check(_lib.dgm_batch_create(ctypes.byref(h), arr, len(self.solvers),
+                                     self.stream.cuda_stream))
+        self.handle = h
+        self._keep = arr
+        self.t = np.zeros(len(self.solvers))
+
+    def advance(self, n_steps, t0=None):
+        t = self.t if t0 is None else np.ascontiguousarray(t0, dtype=np.float64)
+        _check(_lib.dgm_batch_advance(self.handle, int(n_steps), t.ctypes.data))
+        self.t = t + n_steps * np.array([s.dt for s in self.solvers])
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dgm_batch_destroy(self.handle)
+            self.handle = None
+
+
+def receiver_records(solver, eps, mu, n_steps, t0=0.0, u0=None, aux0=None):
+    """Receiver records [n, S, R, 3] as a differentiable function of per-element
+    eps and mu (torch float64 tensors [K]); backward runs the hand-written
+    adjoint kernels with sqrt(N) checkpointing (dgm_forward_record / dgm_adjoint)."""
+    import torch
+
+    class _Records(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, e, m):
+            solver.set_materials(e.detach().cpu().numpy(), m.detach().cpu().numpy())
+            K, S, N = solver.K, solver.S, solver.N
+            solver.set_state(np.zeros((K, S, 6, N)) if u0 is None else u0)
+            if solver.npml:
+                solver.aux[solver.current()].zero_()
+                if aux0 is not None:
+                    solver.aux[solver.current()].copy_(solver.aux_to_device(aux0))
+            ws = solver.adjoint_workspace(n_steps)
+            rec = solver.forward_record(n_steps, t0, ws)
+            ctx.ws = ws
+            return rec
+
+        @staticmethod
+        def backward(ctx, grad):
+            deps, dmu = solver.adjoint(n_steps, t0, grad, ctx.ws)
+            return deps.to(eps.device), dmu.to(mu.device)
+
+    return _Records.apply(eps, mu)
+

@@ -1,0 +1,77 @@
+"""Batched advance (one CUDA graph launch per two steps over several problems)
+against the same problems advanced one by one, and one member against the
+oracle.  Members differ in order, precision, size, columns, PML and sources."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle_ref import build, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_2002_08733_gb300 import build as B, dgmax
+    B.build()
+    dgmax.load_library()
+    return dgmax
+
+
+def _members(D):
+    out = []
+    xyz, tets = W.kuhn_mesh(3, (-1, -1, -1), (1, 1, 1))
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+    srcs = [W.dipole((0.1, 0.05, -0.02), 2.0, 1.0), W.dipole((-0.2, 0.1, 0.15), 3.0, 1.0), None]
+    out.append(dict(args=(xyz, tets, 1.0, 1.0, 2, "fp32", "upwind", "lsrk4", W.stable_dt(2 / 3, 2)),
+                    kw=dict(S=3, pml=pml), srcs=srcs, seed=1))
+    xyz, tets = W.kuhn_mesh(2, jitter=0.1, seed=2)
+    out.append(dict(args=(xyz, tets, 2.0, 1.0, 3, "fp64", "upwind", "lsrk4", W.stable_dt(0.5, 3)),
+                    kw=dict(S=1), srcs=None, seed=2))
+    xyz, tets = W.kuhn_mesh(4)
+    out.append(dict(args=(xyz, tets, 1.0, 1.0, 1, "fp32", "upwind", "lsrk4", W.stable_dt(0.25, 1)),
+                    kw=dict(S=2), srcs=None, seed=3))
+    return out
+
+
+def _make(D, spec):
+    g = D.Solver(*spec["args"], **spec["kw"])
+    if spec["srcs"]:
+        g.set_sources(spec["srcs"])
+    K, p, S = g.K, g.p, g.S
+    g.set_state(W.random_state(K, S, p, seed=spec["seed"]) * 1e-2)
+    return g
+
+
+@pytest.mark.parametrize("steps", [4, 5])
+def test_batch_matches_individual_advance(D, steps):
+    import torch
+    specs = _members(D)
+    batch_members = [_make(D, s) for s in specs]
+    single = [_make(D, s) for s in specs]
+    b = D.Batch(batch_members)
+    b.advance(steps)
+    torch.cuda.synchronize()
+    for gb, gs, spec in zip(batch_members, single, specs):
+        gs.advance(steps, 0.0)
+        tol = 1e-12 if spec["args"][5] == "fp64" else 1e-6
+        assert rel_l2(gb.state(), gs.state()) < tol
+        if gb.npml:
+            a1 = gb.from_device(gb.aux[gb.current()])
+            a2 = gs.from_device(gs.aux[gs.current()])
+            assert rel_l2(a1, a2) < tol
+
+
+def test_batch_member_matches_oracle(D):
+    import torch
+    spec = _members(D)[0]
+    g = _make(D, spec)
+    u0 = g.state()
+    aux0 = np.zeros_like(u0)
+    b = D.Batch([g, _make(D, _members(D)[2])])
+    b.advance(6)
+    torch.cuda.synchronize()
+    xyz, tets, eps, mu, p, prec, flux, integ, dt = spec["args"]
+    o = build(xyz, tets, p, eps, mu, flux, pml=spec["kw"]["pml"], S=3, sources=spec["srcs"])
+    ref, _ = o.unpack(o.lsrk4(o.pack(u0, aux0), 0.0, dt, 6))
+    assert rel_l2(g.state(), ref) < 1e-5
