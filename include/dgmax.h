@@ -201,6 +201,18 @@ int dgm_forward_record(dgm_plan* plan, int64_t n_steps, double t0, double* recor
 int dgm_adjoint(dgm_plan* plan, int64_t n_steps, double t0, const double* drecords_device,
                 void* workspace, double* deps_device, double* dmu_device);
 
+/* Autotuner: times each compiled tile shape (columns per CTA x threads per
+ * CTA) of the LSRK4 stage kernel on the plan's current state, `reps` launches
+ * each, and keeps the fastest for later dgm_advance / dgm_batch_create calls.
+ * The plan's state is not modified: outputs go to `workspace`, device memory
+ * of 2*align256(bytes_fields) + 2*align256(bytes_aux) bytes.  ms_out (host,
+ * may be NULL) receives the mean time per launch of each variant.
+ * Synchronises the bound stream. */
+int dgm_autotune(dgm_plan* plan, void* workspace, int32_t reps, float* ms_out);
+int dgm_autotune_info(const dgm_plan* plan, int32_t* n_variants, int32_t* chosen);
+/* Select a tile-shape variant explicitly (0 .. n_variants-1). */
+int dgm_set_variant(dgm_plan* plan, int32_t variant);
+
 /* Index (0 or 1) of the bound field/aux buffer that holds the current state. */
 int dgm_current(const dgm_plan* plan);
 

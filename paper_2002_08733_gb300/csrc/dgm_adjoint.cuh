@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
     for (int k = grp; k < EG; k += NG)
         eg[k * TE + c] = active ? R(prm.geo[int64_t(k) * K + e]) : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
     for (int i = grp; i < 4 * CH; i += NG) zs[i * TE + c] = 0.0;
+    // the adjoint converts the FP64 geometry itself (FP32 copy passed as geo_r)
     for (int i = grp; i < 2 * 6 * NPART; i += NG) gp[i * TE + c] = 0.0;
     __syncthreads();
     for (int f = grp; f < 4; f += NG) {
@@ -176,13 +177,8 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
         R* fc = fg + f * FGA * TE + c;
-        StageParams sp;
-        sp.geo = prm.geo;
-        sp.nbr = prm.nbr;
-        sp.K = K;
-        sp.upwind = prm.upwind;
         face_constants<R, TE>(f, ait, eg[G_DET * TE + c], eg[G_EPS * TE + c], eg[G_MU * TE + c],
-                              active, sp, e, fc);
+                              active, prm.nbr, static_cast<const R*>(prm.geo_r), K, prm.upwind, e, fc);
         const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
         if (code >= 0 && (code >> 2) < K) {
             const int64_t ne = code >> 2;

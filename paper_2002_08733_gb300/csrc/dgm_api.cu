@@ -65,7 +65,7 @@ struct dgm_plan {
     bool has_pml = false;
     // geometry buffer layout (byte offsets)
     size_t off_geo = 0, off_nbr = 0, off_pml = 0, off_src = 0, off_part = 0, off_status = 0,
-           off_rec = 0, off_time = 0, bytes_geom = 0;
+           off_rec = 0, off_time = 0, off_geo32 = 0, bytes_geom = 0;
     int n_rec = 0;
     std::vector<double> src_host;   // S * (SRC_HDR + 3N)
     bool have_src = false;
@@ -79,6 +79,8 @@ struct dgm_plan {
     cudaStream_t stream = nullptr;
     int cur = 0;
     int device = -1;
+    int variant = 0;          // LSRK stage tile shape chosen by dgm_autotune
+    float variant_ms[8] = {0};
 };
 
 static thread_local std::string g_err;
@@ -227,6 +229,8 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
     size_t off = 0;
     P->off_geo = off;
     off = align256(off + sizeof(double) * G_COUNT * K);
+    P->off_geo32 = off;   // FP32 copy of the geometry for FP32 kernels
+    off = align256(off + sizeof(float) * G_COUNT * K);
     P->off_nbr = off;
     off = align256(off + sizeof(int32_t) * 4 * K);
     P->off_pml = off;
@@ -294,6 +298,13 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
     if ((e = cudaMemcpyAsync(P->geom + P->off_geo, P->mesh.geo.data(), sizeof(double) * G_COUNT * K,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "upload geometry");
+    {
+        std::vector<float> g32(P->mesh.geo.begin(), P->mesh.geo.end());
+        if ((e = cudaMemcpyAsync(P->geom + P->off_geo32, g32.data(), sizeof(float) * G_COUNT * K,
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "upload geometry (FP32)");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
+    }
     if ((e = cudaMemcpyAsync(P->geom + P->off_nbr, P->mesh.nbr.data(), sizeof(int32_t) * 4 * K,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "upload neighbours");
@@ -315,6 +326,8 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
 static void stage_params(dgm_plan* P, StageParams& prm) {
     std::memset(&prm, 0, sizeof(prm));
     prm.geo = reinterpret_cast<const double*>(P->geom + P->off_geo);
+    prm.geo_r = P->kt->real_size == 8 ? static_cast<const void*>(P->geom + P->off_geo)
+                                      : static_cast<const void*>(P->geom + P->off_geo32);
     prm.nbr = reinterpret_cast<const int32_t*>(P->geom + P->off_nbr);
     prm.pml = P->has_pml ? reinterpret_cast<const int32_t*>(P->geom + P->off_pml) : nullptr;
     prm.src = P->have_src ? reinterpret_cast<const double*>(P->geom + P->off_src) : nullptr;
@@ -324,6 +337,7 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.S = P->opt.n_columns;
     prm.upwind = P->opt.flux == DGM_UPWIND;
     prm.dt = P->opt.dt;
+    prm.variant = P->variant;
 }
 
 int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double* pos,
@@ -949,6 +963,10 @@ extern "C" int dgm_set_materials(dgm_plan* P, const double* eps, const double* m
                                     P->mesh.geo.data() + size_t(G_EPS) * K, sizeof(double) * 2 * K,
                                     cudaMemcpyHostToDevice, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "upload materials");
+    std::vector<float> m32(P->mesh.geo.begin() + size_t(G_EPS) * K, P->mesh.geo.begin() + size_t(G_MU + 1) * K);
+    e = cudaMemcpyAsync(P->geom + P->off_geo32 + sizeof(float) * G_EPS * K, m32.data(),
+                        sizeof(float) * 2 * K, cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload materials (FP32)");
     if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "materials sync");
     return DGM_OK;
 }
@@ -1097,6 +1115,7 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
                 ap.raw = ws + L.raw;
                 ap.jumps = ws + L.jmp;
                 ap.geo = prm.geo;
+                ap.geo_r = prm.geo_r;
                 ap.nbr = prm.nbr;
                 ap.pml = prm.pml;
                 ap.status = prm.status;
@@ -1114,5 +1133,80 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
     reduce_columns<<<unsigned((K + 255) / 256), 256, 0, P->stream>>>(gcol, K, Sc, deps, dmu);
     e = cudaGetLastError();
     return e == cudaSuccess ? DGM_OK : cuda_fail(e, "reduce launch");
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times every tile-shape variant of the LSRK stage kernel on the
+// plan's own state (first-stage form: reads u, writes u_out and res into the
+// caller's workspace, so the plan's state is left untouched) and keeps the
+// fastest for dgm_advance and dgm_batch_create.
+extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* ms_out) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!workspace) return fail(DGM_EINVAL, "null workspace");
+    if (reps < 1) reps = 3;
+    dgm_info info;
+    dgm_plan_info(P, &info);
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    const size_t fb = align256(info.bytes_fields), ab = align256(info.bytes_aux);
+    StageParams prm;
+    stage_params(P, prm);
+    prm.u = P->fields[P->cur];
+    prm.aux = P->aux[P->cur];
+    prm.u_out = ws;
+    prm.res = ws + fb;
+    prm.aux_out = ab ? ws + 2 * fb : nullptr;
+    prm.aux_res = ab ? ws + 2 * fb + ab : nullptr;
+    prm.a = 0.0;
+    prm.b = LSRK_B[0];
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < P->kt->n_variants; ++v) {
+        prm.variant = v;
+        int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);   // warm
+        if (rc) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(rc, "stage kernel launch failed");
+        }
+        cudaEventRecord(e0, P->stream);
+        for (int r = 0; r < reps; ++r) P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+        cudaEventRecord(e1, P->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "autotune timing");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (v < 8) P->variant_ms[v] = ms;
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P->variant = best;
+    return DGM_OK;
+}
+
+extern "C" int dgm_autotune_info(const dgm_plan* P, int32_t* n_variants, int32_t* chosen) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (n_variants) *n_variants = P->kt->n_variants;
+    if (chosen) *chosen = P->variant;
+    return DGM_OK;
+}
+
+extern "C" int dgm_set_variant(dgm_plan* P, int32_t v) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (v < 0 || v >= P->kt->n_variants) return fail(DGM_EINVAL, "variant out of range");
+    P->variant = v;
+    return DGM_OK;
 }
 

@@ -41,7 +41,8 @@ struct StageParams {
     const void* aux;      // PML auxiliaries in [6][N][P][S]
     void* aux_out;
     void* aux_res;
-    const double* geo;    // [G_COUNT][K]
+    const double* geo;    // [G_COUNT][K] FP64 master copy
+    const void* geo_r;    // the same in the kernel's real type (FP32 copy for FP32 kernels)
     const int32_t* nbr;   // [4][K]: (neighbour << 2) | neighbour's local face, or -1
     const int32_t* pml;   // [K]: index into aux, or -1 (may be null without PML)
     const double* src;    // [S][SRC_HDR + 3N] or null
@@ -54,6 +55,7 @@ struct StageParams {
     const double* tdev;   // if set: stage time = *tdev + t (device clock of graph replays)
     void* raw;            // MODE_RAW: right-hand side before the mass inverse [6][N][K][S]
     void* jumps;          // MODE_RAW: physical face jumps dE, dH [4][6][NF][K][S]
+    int32_t variant;      // tile-shape variant of the LSRK stage kernel (autotuner)
 };
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms
@@ -68,6 +70,7 @@ struct AdjParams {
     const void* raw;      // forward right-hand side before the mass inverse
     const void* jumps;    // forward physical face jumps
     const double* geo;
+    const void* geo_r;    // geometry in the kernel's real type
     const int32_t* nbr;
     const int32_t* pml;
     int32_t* status;
@@ -84,6 +87,7 @@ struct KernelTable {
     int (*launch_stage)(const StageParams&, int mode, void* stream);
     int real_size;
     int (*launch_adjoint)(const AdjParams&, void* stream);
+    int n_variants;   // tile-shape variants of the LSRK stage (autotuner)
 };
 
 const KernelTable* kernel_table(int p, int precision);

@@ -21,8 +21,15 @@ namespace {
 
 constexpr int kP = DGM_P;
 using Real = DGM_REAL;
-constexpr int kTE = sizeof(Real) == 8 ? 16 : 32;   // columns per CTA
-constexpr int kNT = sizeof(Real) == 8 ? 192 : 384;  // threads per CTA
+// tile shape: columns per CTA and threads per CTA (DGM_TE / DGM_NT select an
+// autotuner variant; the defaults are the shapes measured best at p = 3)
+#ifdef DGM_TE
+constexpr int kTE = DGM_TE;
+constexpr int kNT = DGM_NT;
+#else
+constexpr int kTE = sizeof(Real) == 8 ? 16 : 32;
+constexpr int kNT = sizeof(Real) == 8 ? 192 : 384;
+#endif
 
 #ifdef DGM_ADJ
 constexpr int kTEA = sizeof(Real) == 8 ? 16 : 32;

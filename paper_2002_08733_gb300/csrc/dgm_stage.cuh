@@ -58,11 +58,12 @@ enum FaceConst {
     FC_BND = 17   // 1 on a PEC face
 };
 constexpr int EG = 16;   // element constants per column (same slots as G_*)
+constexpr int NBS = 4;   // neighbour codes per column staged in shared memory
 
 template <int P, typename R, int TE>
 __host__ __device__ constexpr size_t stage_smem_bytes() {
     return sizeof(R) * size_t(TE) *
-           (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FG + EG);
+           (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FG + EG + NBS);
 }
 
 // Reference operators: straight-line code with literal coefficients generated
@@ -116,9 +117,9 @@ __device__ __forceinline__ double source_time(double t, double f0, double bw, do
 // reference face: (1,1,1), (-1,0,0), (0,-1,0), (0,0,-1).
 template <typename R, int TE>
 __device__ __forceinline__ void face_constants(int f, const R (&ait)[9], R det, R epsm, R mum,
-                                               bool active, const StageParams& prm, int64_t e,
-                                               R* fc) {
-    const int64_t K = prm.K;
+                                               bool active, const int32_t* __restrict__ nbr,
+                                               const R* __restrict__ gr, int64_t K, int upwind,
+                                               int64_t e, R* fc) {
     const R m0 = R(f == 0 ? 1 : (f == 1 ? -1 : 0));
     const R m1 = R(f == 0 ? 1 : (f == 2 ? -1 : 0));
     const R m2 = R(f == 0 ? 1 : (f == 3 ? -1 : 0));
@@ -130,20 +131,20 @@ __device__ __forceinline__ void face_constants(int f, const R (&ait)[9], R det, 
     for (int r = 0; r < 3; ++r) fc[(FC_N + r) * TE] = vn[r] / fs;
     fc[FC_TWOF * TE] = fabs(det) * fs;
     const R zm = sqrt(mum / epsm);
-    const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
+    const int32_t code = active ? nbr[int64_t(f) * K + e] : -1;
     R zp = zm;
     if (code >= 0 && (code >> 2) < K) {
         const int64_t ne = code >> 2;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = R(prm.geo[int64_t(G_AIT + k) * K + ne]);
-        zp = sqrt(R(prm.geo[int64_t(G_MU) * K + ne]) / R(prm.geo[int64_t(G_EPS) * K + ne]));
+        for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = gr[int64_t(G_AIT + k) * K + ne];
+        zp = sqrt(gr[int64_t(G_MU) * K + ne] / gr[int64_t(G_EPS) * K + ne]);
         fc[FC_BND * TE] = R(0);
     } else {
 #pragma unroll
         for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = ait[k];
         fc[FC_BND * TE] = R(1);
     }
-    if (prm.upwind) {
+    if (upwind) {
         const R ym = R(1) / zm, yp = R(1) / zp;
         fc[FC_CE * TE] = zp / (zm + zp);
         fc[FC_BE * TE] = R(1) / (zm + zp);
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     R* trN = trO + 24 * NF * TE;                 // [4][6][NF][TE]  nbr traces -> rhs [6][N][TE]
     R* fg = trN + 24 * NF * TE;                  // [4][FG][TE]
     R* eg = fg + 4 * FG * TE;                    // [EG][TE]
+    int32_t* nbs = reinterpret_cast<int32_t*>(eg + EG * TE);   // [4][TE] neighbour codes
 
     const int c = threadIdx.x % TE;
     const int grp = threadIdx.x / TE;
@@ -232,6 +234,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     const int64_t e = active ? col / S : 0;
     const int s = active ? int(col - e * S) : 0;
     const R* u = static_cast<const R*>(prm.u);   // may alias u_out (leapfrog)
+    const R* gr = static_cast<const R*>(prm.geo_r);
+    if (grp < 4) nbs[grp * TE + c] = active ? prm.nbr[int64_t(grp) * K + e] : -1;
 
     // ---- phase 1: tile coefficients, element and face constants --------------
     // groups 0..3 compute the face constants of face f = group straight from
@@ -241,25 +245,25 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         const int f = grp;
         R ait[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) ait[k] = active ? R(prm.geo[int64_t(G_AIT + k) * K + e]) : R(k % 4 == 0);
-        const R det = active ? R(prm.geo[int64_t(G_DET) * K + e]) : R(1);
-        const R epsm = active ? R(prm.geo[int64_t(G_EPS) * K + e]) : R(1);
-        const R mum = active ? R(prm.geo[int64_t(G_MU) * K + e]) : R(1);
-        face_constants<R, TE>(f, ait, det, epsm, mum, active, prm, e, fg + f * FG * TE + c);
+        for (int k = 0; k < 9; ++k) ait[k] = active ? gr[int64_t(G_AIT + k) * K + e] : R(k % 4 == 0);
+        const R det = active ? gr[int64_t(G_DET) * K + e] : R(1);
+        const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
+        const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
+        face_constants<R, TE>(f, ait, det, epsm, mum, active, prm.nbr, gr, K, prm.upwind, e, fg + f * FG * TE + c);
     }
     for (int r = grp - FACE_GROUPS; r < 6 * N; r += NG - FACE_GROUPS)
         if (r >= 0) us[r * TE + c] = active ? u[int64_t(r) * C + col] : R(0);
     for (int k = grp; k < EG; k += NG)
-        eg[k * TE + c] = active ? R(prm.geo[int64_t(k) * K + e]) : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
+        eg[k * TE + c] = active ? gr[int64_t(k) * K + e] : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
     if (FACE_GROUPS == 0) {
         for (int f = grp; f < 4; f += NG) {
             R ait[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) ait[k] = active ? R(prm.geo[int64_t(G_AIT + k) * K + e]) : R(k % 4 == 0);
-            const R det = active ? R(prm.geo[int64_t(G_DET) * K + e]) : R(1);
-            const R epsm = active ? R(prm.geo[int64_t(G_EPS) * K + e]) : R(1);
-            const R mum = active ? R(prm.geo[int64_t(G_MU) * K + e]) : R(1);
-            face_constants<R, TE>(f, ait, det, epsm, mum, active, prm, e, fg + f * FG * TE + c);
+            for (int k = 0; k < 9; ++k) ait[k] = active ? gr[int64_t(G_AIT + k) * K + e] : R(k % 4 == 0);
+            const R det = active ? gr[int64_t(G_DET) * K + e] : R(1);
+            const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
+            const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
+            face_constants<R, TE>(f, ait, det, epsm, mum, active, prm.nbr, gr, K, prm.upwind, e, fg + f * FG * TE + c);
         }
     }
     __syncthreads();
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             if (MODE == MODE_LF_E && ncomp < 3) do_nbr = false;
             if (MODE == MODE_LF_H && ncomp >= 3) do_nbr = false;
             int32_t code = -1;
-            if (do_nbr && active) code = prm.nbr[int64_t(nf) * K + e];
+            if (do_nbr) code = nbs[nf * TE + c];
             const int64_t ne = code >> 2;
             const bool has_nbr = do_nbr && code >= 0 && ne < K;
             if (do_nbr && code >= 0 && ne >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
@@ -419,6 +423,19 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
 
     // ---- phase 4: volume curl + lift per (component, row part) -----------------
     R* rh = trN;   // [6][N][TE], the neighbour traces are dead now
+    // The LSRK residual rows this thread updates in phase 5 (same item) are
+    // requested now so that their latency overlaps the phase-4 arithmetic.
+    constexpr int RPF = (N + NPART - 1) / NPART;
+    constexpr bool PREFETCH_RES = (MODE == MODE_LSRK) && (6 * NPART <= NG);
+    R resv[PREFETCH_RES ? RPF : 1];
+    if (PREFETCH_RES && grp < 6 * NPART && active && prm.a != 0.0) {
+        const int comp = grp / NPART, part = grp % NPART;
+        const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
+        const R* __restrict__ res = static_cast<const R*>(prm.res);
+#pragma unroll
+        for (int i = 0; i < RPF; ++i)
+            if (lo + i < hi) resv[i] = res[int64_t(comp * N + lo + i) * C + col];
+    }
     for (int it = grp; it < 6 * NPART; it += NG) {
         const int comp = it / NPART;
         const int part = it % NPART;
@@ -519,8 +536,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         R* __restrict__ auxr = static_cast<R*>(prm.aux_res);
         const R dt = R(prm.dt), ca = R(prm.a), cb = R(prm.b);
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
-#pragma unroll 2
-        for (int l = lo; l < hi; ++l) {
+        // rows l = lo + i with a compile-time i, so that the prefetched
+        // residuals stay in registers
+#pragma unroll
+        for (int i = 0; i < RPF; ++i) {
+            const int l = lo + i;
+            if (l >= hi) break;
             const R r0 = rh[((fb + 0) * N + l) * TE + c];
             const R r1 = rh[((fb + 1) * N + l) * TE + c];
             const R r2 = rh[((fb + 2) * N + l) * TE + c];
@@ -549,7 +570,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             if (MODE == MODE_RHS) {
                 uo[gi] = du;
             } else if (MODE == MODE_LSRK) {
-                const R rr = (ca == R(0) ? R(0) : ca * res[gi]) + dt * du;
+                R rold = R(0);
+                if (ca != R(0)) rold = PREFETCH_RES ? resv[PREFETCH_RES ? i : 0] : res[gi];
+                const R rr = ca * rold + dt * du;
                 res[gi] = rr;
                 uo[gi] = uv + cb * rr;
             } else {

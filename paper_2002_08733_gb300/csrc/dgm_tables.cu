@@ -10,6 +10,8 @@ int launch_p1_f32_lfe(const StageParams&, void*);
 int launch_p1_f32_lfh(const StageParams&, void*);
 int launch_p1_f32_raw(const StageParams&, void*);
 int launch_p1_f32_adj(const AdjParams&, void*);
+int launch_p1_f32_lsrk_v1(const StageParams&, void*);
+int launch_p1_f32_lsrk_v2(const StageParams&, void*);
 int launch_p1_f64_rhs(const StageParams&, void*);
 int launch_p1_f64_lsrk(const StageParams&, void*);
 int launch_p1_f64_lfe(const StageParams&, void*);
@@ -22,6 +24,8 @@ int launch_p2_f32_lfe(const StageParams&, void*);
 int launch_p2_f32_lfh(const StageParams&, void*);
 int launch_p2_f32_raw(const StageParams&, void*);
 int launch_p2_f32_adj(const AdjParams&, void*);
+int launch_p2_f32_lsrk_v1(const StageParams&, void*);
+int launch_p2_f32_lsrk_v2(const StageParams&, void*);
 int launch_p2_f64_rhs(const StageParams&, void*);
 int launch_p2_f64_lsrk(const StageParams&, void*);
 int launch_p2_f64_lfe(const StageParams&, void*);
@@ -34,6 +38,8 @@ int launch_p3_f32_lfe(const StageParams&, void*);
 int launch_p3_f32_lfh(const StageParams&, void*);
 int launch_p3_f32_raw(const StageParams&, void*);
 int launch_p3_f32_adj(const AdjParams&, void*);
+int launch_p3_f32_lsrk_v1(const StageParams&, void*);
+int launch_p3_f32_lsrk_v2(const StageParams&, void*);
 int launch_p3_f64_rhs(const StageParams&, void*);
 int launch_p3_f64_lsrk(const StageParams&, void*);
 int launch_p3_f64_lfe(const StageParams&, void*);
@@ -46,6 +52,8 @@ int launch_p4_f32_lfe(const StageParams&, void*);
 int launch_p4_f32_lfh(const StageParams&, void*);
 int launch_p4_f32_raw(const StageParams&, void*);
 int launch_p4_f32_adj(const AdjParams&, void*);
+int launch_p4_f32_lsrk_v1(const StageParams&, void*);
+int launch_p4_f32_lsrk_v2(const StageParams&, void*);
 int launch_p4_f64_rhs(const StageParams&, void*);
 int launch_p4_f64_lsrk(const StageParams&, void*);
 int launch_p4_f64_lfe(const StageParams&, void*);
@@ -58,13 +66,18 @@ int launch_p5_f32_lfe(const StageParams&, void*);
 int launch_p5_f32_lfh(const StageParams&, void*);
 int launch_p5_f32_raw(const StageParams&, void*);
 int launch_p5_f32_adj(const AdjParams&, void*);
+int launch_p5_f32_lsrk_v1(const StageParams&, void*);
+int launch_p5_f32_lsrk_v2(const StageParams&, void*);
 
 namespace {
 
 int launch_p1_f32(const StageParams& prm, int mode, void* st) {
     switch (mode) {
         case MODE_RHS: return launch_p1_f32_rhs(prm, st);
-        case MODE_LSRK: return launch_p1_f32_lsrk(prm, st);
+        case MODE_LSRK:
+            if (prm.variant == 1) return launch_p1_f32_lsrk_v1(prm, st);
+            if (prm.variant == 2) return launch_p1_f32_lsrk_v2(prm, st);
+            return launch_p1_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p1_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p1_f32_lfh(prm, st);
         case MODE_RAW: return launch_p1_f32_raw(prm, st);
@@ -86,7 +99,10 @@ int launch_p1_f64(const StageParams& prm, int mode, void* st) {
 int launch_p2_f32(const StageParams& prm, int mode, void* st) {
     switch (mode) {
         case MODE_RHS: return launch_p2_f32_rhs(prm, st);
-        case MODE_LSRK: return launch_p2_f32_lsrk(prm, st);
+        case MODE_LSRK:
+            if (prm.variant == 1) return launch_p2_f32_lsrk_v1(prm, st);
+            if (prm.variant == 2) return launch_p2_f32_lsrk_v2(prm, st);
+            return launch_p2_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p2_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p2_f32_lfh(prm, st);
         case MODE_RAW: return launch_p2_f32_raw(prm, st);
@@ -108,7 +124,10 @@ int launch_p2_f64(const StageParams& prm, int mode, void* st) {
 int launch_p3_f32(const StageParams& prm, int mode, void* st) {
     switch (mode) {
         case MODE_RHS: return launch_p3_f32_rhs(prm, st);
-        case MODE_LSRK: return launch_p3_f32_lsrk(prm, st);
+        case MODE_LSRK:
+            if (prm.variant == 1) return launch_p3_f32_lsrk_v1(prm, st);
+            if (prm.variant == 2) return launch_p3_f32_lsrk_v2(prm, st);
+            return launch_p3_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p3_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p3_f32_lfh(prm, st);
         case MODE_RAW: return launch_p3_f32_raw(prm, st);
@@ -130,7 +149,10 @@ int launch_p3_f64(const StageParams& prm, int mode, void* st) {
 int launch_p4_f32(const StageParams& prm, int mode, void* st) {
     switch (mode) {
         case MODE_RHS: return launch_p4_f32_rhs(prm, st);
-        case MODE_LSRK: return launch_p4_f32_lsrk(prm, st);
+        case MODE_LSRK:
+            if (prm.variant == 1) return launch_p4_f32_lsrk_v1(prm, st);
+            if (prm.variant == 2) return launch_p4_f32_lsrk_v2(prm, st);
+            return launch_p4_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p4_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p4_f32_lfh(prm, st);
         case MODE_RAW: return launch_p4_f32_raw(prm, st);
@@ -152,7 +174,10 @@ int launch_p4_f64(const StageParams& prm, int mode, void* st) {
 int launch_p5_f32(const StageParams& prm, int mode, void* st) {
     switch (mode) {
         case MODE_RHS: return launch_p5_f32_rhs(prm, st);
-        case MODE_LSRK: return launch_p5_f32_lsrk(prm, st);
+        case MODE_LSRK:
+            if (prm.variant == 1) return launch_p5_f32_lsrk_v1(prm, st);
+            if (prm.variant == 2) return launch_p5_f32_lsrk_v2(prm, st);
+            return launch_p5_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p5_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p5_f32_lfh(prm, st);
         case MODE_RAW: return launch_p5_f32_raw(prm, st);
@@ -162,14 +187,14 @@ int launch_p5_f32(const StageParams& prm, int mode, void* st) {
 
 }  // namespace
 
-extern const KernelTable kernels_p1_f32 = {launch_p1_f32, 4, launch_p1_f32_adj};
-extern const KernelTable kernels_p1_f64 = {launch_p1_f64, 8, launch_p1_f64_adj};
-extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4, launch_p2_f32_adj};
-extern const KernelTable kernels_p2_f64 = {launch_p2_f64, 8, launch_p2_f64_adj};
-extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4, launch_p3_f32_adj};
-extern const KernelTable kernels_p3_f64 = {launch_p3_f64, 8, launch_p3_f64_adj};
-extern const KernelTable kernels_p4_f32 = {launch_p4_f32, 4, launch_p4_f32_adj};
-extern const KernelTable kernels_p4_f64 = {launch_p4_f64, 8, launch_p4_f64_adj};
-extern const KernelTable kernels_p5_f32 = {launch_p5_f32, 4, launch_p5_f32_adj};
+extern const KernelTable kernels_p1_f32 = {launch_p1_f32, 4, launch_p1_f32_adj, 3};
+extern const KernelTable kernels_p1_f64 = {launch_p1_f64, 8, launch_p1_f64_adj, 1};
+extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4, launch_p2_f32_adj, 3};
+extern const KernelTable kernels_p2_f64 = {launch_p2_f64, 8, launch_p2_f64_adj, 1};
+extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4, launch_p3_f32_adj, 3};
+extern const KernelTable kernels_p3_f64 = {launch_p3_f64, 8, launch_p3_f64_adj, 1};
+extern const KernelTable kernels_p4_f32 = {launch_p4_f32, 4, launch_p4_f32_adj, 3};
+extern const KernelTable kernels_p4_f64 = {launch_p4_f64, 8, launch_p4_f64_adj, 1};
+extern const KernelTable kernels_p5_f32 = {launch_p5_f32, 4, launch_p5_f32_adj, 3};
 
 }  // namespace dgm

@@ -72,6 +72,9 @@ _SIGS = {
     "dgm_project": [_P, _P, ctypes.c_int32, _P],
     "dgm_status_check": [_P],
     "dgm_set_materials": [_P, _P, _P],
+    "dgm_autotune": [_P, _P, ctypes.c_int32, _P],
+    "dgm_autotune_info": [_P, _P, _P],
+    "dgm_set_variant": [_P, ctypes.c_int32],
     "dgm_adjoint_workspace": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
     "dgm_forward_record": [_P, ctypes.c_int64, ctypes.c_double, _P, _P],
     "dgm_adjoint": [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
@@ -305,6 +308,22 @@ class Solver(Plan):
                                    device=self.device)
         _check(_lib.dgm_sample_receivers(self.handle, _ptr(f), _ptr(out)))
         return out
+
+    def autotune(self, reps=3):
+        """Pick the fastest tile shape of the LSRK4 stage kernel; returns (chosen, ms per variant)."""
+        nb = 2 * (-(-self.info.bytes_fields // 256) * 256) + 2 * (-(-self.info.bytes_aux // 256) * 256)
+        buf = self.torch.empty(nb + 256, dtype=self.torch.uint8, device=self.device)
+        off = (-buf.data_ptr()) % 256
+        nv, ch = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.dgm_autotune_info(self.handle, ctypes.byref(nv), ctypes.byref(ch)))
+        ms = np.zeros(nv.value, dtype=np.float32)
+        _check(_lib.dgm_autotune(self.handle, buf.data_ptr() + off, int(reps), ms.ctypes.data))
+        _check(_lib.dgm_autotune_info(self.handle, ctypes.byref(nv), ctypes.byref(ch)))
+        del buf
+        return ch.value, ms
+
+    def set_variant(self, v):
+        _check(_lib.dgm_set_variant(self.handle, int(v)))
 
     def set_materials(self, eps, mu):
         eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (self.K,)))

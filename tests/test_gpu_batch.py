@@ -75,3 +75,23 @@ def test_batch_member_matches_oracle(D):
     o = build(xyz, tets, p, eps, mu, flux, pml=spec["kw"]["pml"], S=3, sources=spec["srcs"])
     ref, _ = o.unpack(o.lsrk4(o.pack(u0, aux0), 0.0, dt, 6))
     assert rel_l2(g.state(), ref) < 1e-5
+
+
+def test_autotuned_variants_match_oracle(D):
+    """Every tile-shape variant the autotuner may pick gives the same stage."""
+    import torch
+    xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=71)
+    K, p, S = len(tets), 3, 3
+    u = W.random_state(K, S, p, seed=72)
+    dt = W.stable_dt(1 / 3, p)
+    o = build(xyz, tets, p, 1.0, 1.0, "upwind", S=S)
+    ref = o.unpack(o.lsrk4(o.pack(u), 0.0, dt, 3))[0]
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", dt, S=S)
+    chosen, ms = g.autotune()
+    assert len(ms) == 3 and 0 <= chosen < 3 and np.all(ms > 0)
+    for v in range(3):
+        g2 = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", dt, S=S)
+        g2.set_state(u)
+        g2.set_variant(v)
+        g2.advance(3)
+        assert rel_l2(g2.state(), ref) < 1e-5

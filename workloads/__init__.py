@@ -199,3 +199,31 @@ def dipole(pos, f0, bw, direction=(0.0, 0.0, 1.0)):
     bandwidth bw and envelope delay t0 = 4 s with s = 1/(2 pi bw)."""
     return dict(pos=tuple(float(v) for v in pos), dir=tuple(float(v) for v in direction),
                 f0=float(f0), bw=float(bw), t0=4.0 / (2.0 * math.pi * bw))
+
+
+def batched_sources_and_cavities(seed=2004, n_sources=64, n_cavities=16, n=24, p=3):
+    """Batch of many dipole excitations sharing one PML mesh plus uneven cavities.
+
+    Sources: [-1,1]^3 on an n^3 Kuhn grid, degree p, PML 0.25 thick (quadratic
+    profile, sigma_max 40), n_sources z-dipoles at seeded interior positions
+    with f0 seeded in [1, 4] (bandwidth 1), one per batch column.
+    Cavities: unit-cube PEC cavities with n_i seeded in 6..28 and p_i in 2..5,
+    vacuum, each with its own dt = 0.3 h_i / (p_i+1)^2, TM110 initial field.
+    Upwind flux and LSRK4 everywhere.
+    """
+    rng = np.random.default_rng(seed)
+    w = dipole_pml(n=n, p=p, seed=seed)
+    inner = 1 - w.pml["thickness"]
+    h = 2.0 / n
+    w.S = n_sources
+    w.extra["sources"] = [dipole(rng.uniform(-inner + 2 * h, inner - 2 * h, size=3),
+                                 rng.uniform(1.0, 4.0), 1.0) for _ in range(n_sources)]
+    cav = []
+    for _ in range(n_cavities):
+        ni = int(rng.integers(6, 29))
+        pi = int(rng.integers(2, 6))
+        c = Workload("cavity_n%d_p%d" % (ni, pi), ni, (0, 0, 0), (1, 1, 1), pi, "upwind",
+                     "lsrk4", 0, stable_dt(1.0 / ni, pi))
+        cav.append(c)
+    return w, cav
+
