@@ -126,10 +126,10 @@ def stage_bytes(K, N, S, real_size):
     """Algorithmic DRAM bytes of one LSRK4 step (five stage launches).
 
     Per stage: read u, write u_out, write res (and read res except in the first
-    stage, whose coefficient a_1 = 0), plus per element the FP64 geometry
-    record (16 doubles) and the neighbour table (4 int32)."""
+    stage, whose coefficient a_1 = 0), plus per element the geometry record
+    (16 reals in the kernel's precision) and the neighbour table (4 int32)."""
     field = 6 * N * K * S * real_size
-    geo = K * (16 * 8 + 4 * 4)
+    geo = K * (16 * real_size + 4 * 4)
     return (3 * field + geo) + 4 * (4 * field + geo)
 
 
@@ -148,7 +148,10 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     K, N, S = g.K, g.N, g.S
     dofs = 6 * N * K * S
     tuned = None
-    if precision == "fp32":
+    if precision == "fp32" and args.variant is not None:
+        g.set_variant(args.variant)
+        tuned = {"variant": int(args.variant), "forced": True}
+    elif precision == "fp32":
         v, ms = g.autotune()
         tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms],
                  "variants": ["32 cols x 384 thr", "32 cols x 192 thr", "16 cols x 192 thr"]}
@@ -216,15 +219,17 @@ def run_pml(precision, steps, warmup, n=40):
         ev1.synchronize()
         ms = ev0.elapsed_time(ev1)
         g.status()
+    final = g.fields[g.current()].double().cpu()
     dofs = 6 * g.N * g.K
     rs = g.info.real_size
     field = 6 * g.N * g.K * rs
     aux = 6 * g.N * g.npml * rs
-    geo = g.K * (16 * 8 + 4 * 4 + 4)
+    geo = g.K * (16 * rs + 4 * 4 + 4)
     step_bytes = (3 * field + 3 * aux + geo) + 4 * (4 * field + 4 * aux + geo)
     return dict(value=dofs * steps / (ms * 1e-3), ms_per_step=ms / steps, steps=steps, K=g.K,
                 N=g.N, n_pml=g.npml, bytes_per_step=step_bytes,
-                hbm_frac=step_bytes / (ms / steps * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0))
+                hbm_frac=step_bytes / (ms / steps * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0),
+                _final=final)
 
 
 def run_batched(steps, warmup):
@@ -271,6 +276,41 @@ def run_batched(steps, warmup):
                 members=len(members), dofs_per_step=dofs, sources=w.S,
                 cavities=[(c.n, c.p) for c in cavs], variants=chosen,
                 graph_launches=steps // 2)
+
+
+def run_adjoint(steps):
+    """Inverse-problem workload: forward with receiver records plus the
+    hand-written adjoint (sqrt(N) checkpointing), FP32 state, FP64 gradient."""
+    import torch
+    from paper_2002_08733_gb300 import dgmax as D
+    w = W.inverse_problem(steps=steps)
+    xyz, tets = w.mesh()
+    dev = torch.device("cuda", 0)
+    rec = w.extra["receivers"]
+    g = D.Solver(xyz, tets, w.extra["eps_target"], 1.0, w.p, "fp32", w.flux, w.integrator, w.dt,
+                 device=dev, S=w.S, pml=w.pml, max_receivers=len(rec))
+    g.set_sources(w.extra["sources"])
+    g.set_receivers(rec)
+    mu = torch.ones(g.K, dtype=torch.float64)
+    with torch.no_grad():
+        target = D.receiver_records(g, torch.tensor(w.extra["eps_target"]), mu, steps)
+    eps = torch.tensor(w.extra["eps"], requires_grad=True)
+    mu_p = mu.clone().requires_grad_(True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r = D.receiver_records(g, eps, mu_p, steps)
+    loss = 0.5 * ((r - target) ** 2).sum()
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    dofs = 6 * g.N * g.K * g.S
+    return dict(steps=steps, K=g.K, S=g.S, receivers=len(rec), loss=float(loss.detach()),
+                forward_s=t1 - t0, adjoint_s=t2 - t1,
+                forward_dof_updates_per_s=dofs * steps / (t1 - t0),
+                adjoint_over_forward=(t2 - t1) / (t1 - t0),
+                grad_eps_norm=float(eps.grad.norm()), grad_mu_norm=float(mu_p.grad.norm()))
 
 
 def run_e2e(g, steps, t0):
@@ -334,6 +374,11 @@ def main():
     ap.add_argument("--no-pml", action="store_true", help="skip the p=4 dipole-in-PML workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
     ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the inverse-problem workload")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="force the FP32 stage-kernel tile shape instead of autotuning "
+                         "(profiling runs: the autotuner's timings are distorted under ncu)")
+    ap.add_argument("--adjoint-steps", type=int, default=60)
     ap.add_argument("--pml-steps", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -429,15 +474,23 @@ def main():
     }
     if not args.no_pml and world == 1:
         p32 = run_pml("fp32", args.pml_steps, 3)
-        p64 = run_pml("fp64", max(2, args.pml_steps // 5), 1)
+        p64 = run_pml("fp64", args.pml_steps, 3)
+        f32, f64 = p32.pop("_final"), p64.pop("_final")
+        err = float((f32 - f64).norm() / f64.norm())
         line["p4_pml"] = {"workload": "dipole_pml: [-1,1]^3, 40^3 Kuhn grid, 384000 tets, p=4, "
-                                      "PML 0.25 sigma_max=40, z dipole, upwind, LSRK4",
-                          "fp32": p32, "fp64": p64, "fp32_over_fp64": p32["value"] / p64["value"]}
+                                      "PML 0.25 sigma_max=40, z dipole, upwind, LSRK4, from rest",
+                          "fp32": p32, "fp64": p64, "fp32_over_fp64": p32["value"] / p64["value"],
+                          "fp32_vs_fp64_rel_l2_after_%d_steps" % (args.pml_steps + 3): err}
     if not args.no_batched and world == 1:
         line["batched"] = dict(workload="64 dipoles on a 24^3 PML mesh (p=3, S=64) + 16 PEC "
                                         "cavities n 6..28, p 2..5; FP32; one graph launch per "
                                         "two steps; autotuned tile shapes",
                                **run_batched(args.batched_steps, 2))
+    if not args.no_adjoint and world == 1:
+        line["adjoint"] = dict(workload="24^3 PML mesh (82944 tets), p=3, 8 dipoles, 32 "
+                                        "receivers, lognormal eps, receiver-misfit loss; FP32 "
+                                        "state, FP64 gradient, sqrt(N) checkpoints",
+                               **run_adjoint(args.adjoint_steps))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, _ = cpu_reference(seconds_budget=15.0)
         line["cpu_baseline"] = base

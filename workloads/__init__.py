@@ -227,3 +227,21 @@ def batched_sources_and_cavities(seed=2004, n_sources=64, n_cavities=16, n=24, p
         cav.append(c)
     return w, cav
 
+
+def inverse_problem(seed=2005, n=24, p=3, n_sources=8, n_receivers=32, steps=1500):
+    """Differentiable inverse problem: [-1,1]^3 on an n^3 Kuhn grid with a PML
+    (0.25 thick, quadratic, sigma_max 40), degree p, per-element eps lognormal
+    (median 2, sigma 0.3), mu = 1, n_sources z-dipoles (one per column) and
+    n_receivers receiver points in the interior, a seeded target eps field."""
+    rng = np.random.default_rng(seed)
+    w = dipole_pml(n=n, p=p, seed=seed, steps=steps)
+    inner = 1 - w.pml["thickness"]
+    h = 2.0 / n
+    w.S = n_sources
+    w.extra["sources"] = [dipole(rng.uniform(-inner + 2 * h, inner - 2 * h, size=3),
+                                 rng.uniform(1.0, 4.0), 1.0) for _ in range(n_sources)]
+    w.extra["receivers"] = rng.uniform(-inner + h, inner - h, size=(n_receivers, 3))
+    w.extra["eps"] = lognormal_material(w.K, 2.0, 0.3, seed + 1)
+    w.extra["eps_target"] = lognormal_material(w.K, 2.0, 0.3, seed + 2)
+    return w
+
