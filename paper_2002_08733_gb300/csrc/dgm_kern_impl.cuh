@@ -12,6 +12,8 @@
 
 #ifdef DGM_ADJ
 #include "dgm_adjoint.cuh"
+#elif defined(DGM_PAIR)
+#include "dgm_stage2.cuh"
 #else
 #include "dgm_stage.cuh"
 #endif
@@ -48,6 +50,25 @@ int launch_adj(const AdjParams& prm, cudaStream_t st) {
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + kTEA - 1) / kTEA);
     k<<<grid, kNTA, smem, st>>>(prm);
+    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+}
+#elif defined(DGM_PAIR)
+// paired kernel: 64 columns per CTA, two per thread (LSRK stages only)
+int launch_mode(const StageParams& prm, cudaStream_t st) {
+    using Pair = DGM_PAIR;
+    constexpr size_t smem = stage2_smem_bytes<kP, Pair>();
+    static bool configured = false;
+    auto k = stage2_kernel<kP, Pair, kNT>;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+            cudaSuccess)
+            return DGM_ECUDA;
+        configured = true;
+    }
+    const int64_t C = prm.K * prm.S;
+    if (C <= 0) return DGM_OK;
+    const unsigned grid = unsigned((C + 63) / 64);
+    k<<<grid, kNT, smem, st>>>(prm);
     return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
 }
 #else

@@ -35,6 +35,9 @@ int main(int argc, char** argv) {
     if (!f) return 1;
     std::fprintf(f, "// Generated by dgm_refgen.cpp at build time; do not edit.\n#pragma once\n\n");
     std::fprintf(f, "namespace dgm {\n\n");
+    std::fprintf(f, "// fused multiply-add used by the operators (overloaded per real type)\n");
+    std::fprintf(f, "__device__ __forceinline__ float fmaa(float a, float b, float c) { return fmaf(a, b, c); }\n");
+    std::fprintf(f, "__device__ __forceinline__ double fmaa(double a, double b, double c) { return fma(a, b, c); }\n\n");
     std::fprintf(f, "template <int P, int F> struct TraceOp;\ntemplate <int P, int F> struct LiftOp;\n");
     std::fprintf(f, "template <int P, int A> struct DerivOp;\ntemplate <int P, int A> struct DerivTOp;\n");
     std::fprintf(f, "template <int P> struct RefNnz;\n\n");
@@ -62,16 +65,24 @@ int main(int argc, char** argv) {
             std::fprintf(f, "template <> struct TraceOp<%d, %d> {\n  template <typename R>\n"
                             "  __device__ static __forceinline__ void apply(const R* v, R* acc) {\n", p, fc);
             for (int m = 0; m < NF; ++m) {
-                std::fprintf(f, "    acc[%d] = R(0)", m);
+                bool first = true;
                 for (int l = 0; l < N; ++l) {
                     double c = rv(fc, m, l);
                     if (c == 0.0) continue;
                     ++nnzR;
-                    std::fprintf(f, " + ");
-                    lit(f, c);
-                    std::fprintf(f, " * v[%d]", l);
+                    if (first) {
+                        std::fprintf(f, "    acc[%d] = ", m);
+                        lit(f, c);
+                        std::fprintf(f, " * v[%d];", l);
+                        first = false;
+                    } else {
+                        std::fprintf(f, " acc[%d] = fmaa(", m);
+                        lit(f, c);
+                        std::fprintf(f, ", v[%d], acc[%d]);", l, m);
+                    }
                 }
-                std::fprintf(f, ";\n");
+                if (first) std::fprintf(f, "    acc[%d] = R(0);", m);
+                std::fprintf(f, "\n");
             }
             std::fprintf(f, "  }\n};\n");
             std::fprintf(f, "template <> struct LiftOp<%d, %d> {\n  template <typename R, int LO = 0, int HI = %d>\n"
@@ -86,9 +97,9 @@ int main(int argc, char** argv) {
                 for (int l = 0; l < N; ++l) {
                     double c = rv(fc, m, l);
                     if (c == 0.0) continue;
-                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] += ", l, l, l);
+                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] = fmaa(", l, l, l);
                     lit(f, c);
-                    std::fprintf(f, " * x;");
+                    std::fprintf(f, ", x, acc[%d]);", l);
                 }
                 std::fprintf(f, " }\n");
             }
@@ -108,9 +119,9 @@ int main(int argc, char** argv) {
                     double c = sv(a, l, m);
                     if (c == 0.0) continue;
                     ++nnzS;
-                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] += ", l, l, l);
+                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] = fmaa(", l, l, l);
                     lit(f, c);
-                    std::fprintf(f, " * x;");
+                    std::fprintf(f, ", x, acc[%d]);", l);
                 }
                 std::fprintf(f, " }\n");
             }
@@ -130,9 +141,9 @@ int main(int argc, char** argv) {
                 for (int m = 0; m < N; ++m) {
                     double c = sv(a, l, m);
                     if (c == 0.0) continue;
-                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] += ", m, m, m);
+                    std::fprintf(f, " if (LO <= %d && %d < HI) acc[%d] = fmaa(", m, m, m);
                     lit(f, c);
-                    std::fprintf(f, " * x;");
+                    std::fprintf(f, ", x, acc[%d]);", m);
                 }
                 std::fprintf(f, " }\n");
             }

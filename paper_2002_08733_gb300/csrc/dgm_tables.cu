@@ -1,4 +1,8 @@
 // Dispatch tables over the per-(degree, precision, mode) kernel modules.
+// FP32 LSRK stage variants for the autotuner: 0 = 32 columns x 384 threads,
+// 1 = 32 x 192, 2 = 16 x 192, and up to p = 3 (where 64 columns of pairs fit
+// in shared memory) 3 = paired kernel with packed FP32x2 arithmetic,
+// 4 = paired kernel with scalar arithmetic.
 #include "dgm_internal.h"
 #include "dgmax.h"
 
@@ -12,6 +16,8 @@ int launch_p1_f32_raw(const StageParams&, void*);
 int launch_p1_f32_adj(const AdjParams&, void*);
 int launch_p1_f32_lsrk_v1(const StageParams&, void*);
 int launch_p1_f32_lsrk_v2(const StageParams&, void*);
+int launch_p1_f32_lsrk_v3(const StageParams&, void*);
+int launch_p1_f32_lsrk_v4(const StageParams&, void*);
 int launch_p1_f64_rhs(const StageParams&, void*);
 int launch_p1_f64_lsrk(const StageParams&, void*);
 int launch_p1_f64_lfe(const StageParams&, void*);
@@ -26,6 +32,8 @@ int launch_p2_f32_raw(const StageParams&, void*);
 int launch_p2_f32_adj(const AdjParams&, void*);
 int launch_p2_f32_lsrk_v1(const StageParams&, void*);
 int launch_p2_f32_lsrk_v2(const StageParams&, void*);
+int launch_p2_f32_lsrk_v3(const StageParams&, void*);
+int launch_p2_f32_lsrk_v4(const StageParams&, void*);
 int launch_p2_f64_rhs(const StageParams&, void*);
 int launch_p2_f64_lsrk(const StageParams&, void*);
 int launch_p2_f64_lfe(const StageParams&, void*);
@@ -40,6 +48,8 @@ int launch_p3_f32_raw(const StageParams&, void*);
 int launch_p3_f32_adj(const AdjParams&, void*);
 int launch_p3_f32_lsrk_v1(const StageParams&, void*);
 int launch_p3_f32_lsrk_v2(const StageParams&, void*);
+int launch_p3_f32_lsrk_v3(const StageParams&, void*);
+int launch_p3_f32_lsrk_v4(const StageParams&, void*);
 int launch_p3_f64_rhs(const StageParams&, void*);
 int launch_p3_f64_lsrk(const StageParams&, void*);
 int launch_p3_f64_lfe(const StageParams&, void*);
@@ -77,6 +87,8 @@ int launch_p1_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK:
             if (prm.variant == 1) return launch_p1_f32_lsrk_v1(prm, st);
             if (prm.variant == 2) return launch_p1_f32_lsrk_v2(prm, st);
+            if (prm.variant == 3) return launch_p1_f32_lsrk_v3(prm, st);
+            if (prm.variant == 4) return launch_p1_f32_lsrk_v4(prm, st);
             return launch_p1_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p1_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p1_f32_lfh(prm, st);
@@ -102,6 +114,8 @@ int launch_p2_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK:
             if (prm.variant == 1) return launch_p2_f32_lsrk_v1(prm, st);
             if (prm.variant == 2) return launch_p2_f32_lsrk_v2(prm, st);
+            if (prm.variant == 3) return launch_p2_f32_lsrk_v3(prm, st);
+            if (prm.variant == 4) return launch_p2_f32_lsrk_v4(prm, st);
             return launch_p2_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p2_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p2_f32_lfh(prm, st);
@@ -127,6 +141,8 @@ int launch_p3_f32(const StageParams& prm, int mode, void* st) {
         case MODE_LSRK:
             if (prm.variant == 1) return launch_p3_f32_lsrk_v1(prm, st);
             if (prm.variant == 2) return launch_p3_f32_lsrk_v2(prm, st);
+            if (prm.variant == 3) return launch_p3_f32_lsrk_v3(prm, st);
+            if (prm.variant == 4) return launch_p3_f32_lsrk_v4(prm, st);
             return launch_p3_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p3_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p3_f32_lfh(prm, st);
@@ -187,11 +203,11 @@ int launch_p5_f32(const StageParams& prm, int mode, void* st) {
 
 }  // namespace
 
-extern const KernelTable kernels_p1_f32 = {launch_p1_f32, 4, launch_p1_f32_adj, 3};
+extern const KernelTable kernels_p1_f32 = {launch_p1_f32, 4, launch_p1_f32_adj, 5};
 extern const KernelTable kernels_p1_f64 = {launch_p1_f64, 8, launch_p1_f64_adj, 1};
-extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4, launch_p2_f32_adj, 3};
+extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4, launch_p2_f32_adj, 5};
 extern const KernelTable kernels_p2_f64 = {launch_p2_f64, 8, launch_p2_f64_adj, 1};
-extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4, launch_p3_f32_adj, 3};
+extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4, launch_p3_f32_adj, 5};
 extern const KernelTable kernels_p3_f64 = {launch_p3_f64, 8, launch_p3_f64_adj, 1};
 extern const KernelTable kernels_p4_f32 = {launch_p4_f32, 4, launch_p4_f32_adj, 3};
 extern const KernelTable kernels_p4_f64 = {launch_p4_f64, 8, launch_p4_f64_adj, 1};

@@ -78,7 +78,10 @@ def test_batch_member_matches_oracle(D):
 
 
 def test_autotuned_variants_match_oracle(D):
-    """Every tile-shape variant the autotuner may pick gives the same stage."""
+    """Every tile-shape variant the autotuner may pick gives the same stage:
+    three single-column shapes and, up to p = 3, the paired kernels (two columns
+    per thread, packed FP32x2 and scalar arithmetic).  486 columns leave a
+    ragged last tile for every shape."""
     import torch
     xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=71)
     K, p, S = len(tets), 3, 3
@@ -88,10 +91,42 @@ def test_autotuned_variants_match_oracle(D):
     ref = o.unpack(o.lsrk4(o.pack(u), 0.0, dt, 3))[0]
     g = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", dt, S=S)
     chosen, ms = g.autotune()
-    assert len(ms) == 3 and 0 <= chosen < 3 and np.all(ms > 0)
-    for v in range(3):
+    assert len(ms) == 5 and 0 <= chosen < 5 and np.all(ms > 0)
+    for v in range(5):
         g2 = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", dt, S=S)
         g2.set_state(u)
         g2.set_variant(v)
         g2.advance(3)
-        assert rel_l2(g2.state(), ref) < 1e-5
+        assert rel_l2(g2.state(), ref) < 1e-5, v
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("v", [3, 4])
+def test_paired_variants_pml_sources_match_oracle(D, p, v):
+    """Paired kernels on a problem where the two columns of a thread differ:
+    PML and non-PML elements, elements with and without a source, jittered
+    geometry with element-wise materials, S = 3 columns per element (the last
+    without a source)."""
+    import torch
+    xyz, tets = W.kuhn_mesh(3, (-1, -1, -1), (1, 1, 1), jitter=0.1, seed=80 + p)
+    K = len(tets)
+    rng = np.random.default_rng(90 + p)
+    eps = rng.uniform(1.0, 3.0, K)
+    mu = rng.uniform(1.0, 2.0, K)
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+    srcs = [W.dipole((0.1, 0.05, -0.02), 2.0, 1.0), W.dipole((-0.2, 0.1, 0.15), 3.0, 1.0), None]
+    S = 3
+    dt = W.stable_dt(2 / 3, p)
+    g = D.Solver(xyz, tets, eps, mu, p, "fp32", "upwind", "lsrk4", dt, S=S, pml=pml)
+    g.set_sources(srcs)
+    g.set_variant(v)
+    u0 = W.random_state(K, S, p, seed=100 + p) * 1e-2
+    g.set_state(u0)
+    g.advance(4)
+    torch.cuda.synchronize()
+    o = build(xyz, tets, p, eps, mu, "upwind", pml=pml, S=S, sources=srcs)
+    aux0 = np.zeros((K, S, 6, u0.shape[-1]))
+    ref_u, ref_aux = o.unpack(o.lsrk4(o.pack(u0, aux0), 0.0, dt, 4))
+    assert rel_l2(g.state(), ref_u) < 2e-5
+    a = g.from_device(g.aux[g.current()])
+    assert rel_l2(a, ref_aux[g.pml_elements()]) < 2e-5
