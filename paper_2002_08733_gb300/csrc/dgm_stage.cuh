@@ -238,9 +238,20 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     if (grp < 4) nbs[grp * TE + c] = active ? prm.nbr[int64_t(grp) * K + e] : -1;
 
     // ---- phase 1: tile coefficients, element and face constants --------------
-    // groups 0..3 compute the face constants of face f = group straight from
-    // global memory while the other groups stage the tile's coefficients
+    // Groups 0..3 compute the face constants of face f = group straight from
+    // global memory (two dependent round trips: neighbour code, then the
+    // neighbour's geometry).  The other groups stage the tile's coefficients
+    // and element constants, each thread issuing all its loads before its
+    // first shared-memory store, and request the neighbour coefficients of
+    // their first phase-2 item, so that every global round trip of the tile
+    // is in flight at once.
     constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
+    constexpr int LG = NG - FACE_GROUPS;                 // loading groups
+    R vn[N];                                            // neighbour coefficients (phase 2)
+    bool vn_ready = false;                              // round-0 item prefetched in phase 1
+    auto nbr_item_active = [&](int comp) {
+        return !((MODE == MODE_LF_E && comp < 3) || (MODE == MODE_LF_H && comp >= 3));
+    };
     if (grp < FACE_GROUPS) {
         const int f = grp;
         R ait[9];
@@ -250,11 +261,49 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
         const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
         face_constants<R, TE>(f, ait, det, epsm, mum, active, prm.nbr, gr, K, prm.upwind, e, fg + f * FG * TE + c);
+    } else {
+        const int lg = grp - FACE_GROUPS;
+        // round-0 neighbour item of this group: face ni / 6, component ni % 6
+        if (grp < 24 && nbr_item_active(grp % 6) && active) {
+            const int32_t code = prm.nbr[int64_t(grp / 6) * K + e];
+            const int64_t ne = code >> 2;
+            if (code >= 0 && ne < K) {
+                const int64_t ncol = ne * S + s;
+#pragma unroll
+                for (int l = 0; l < N; ++l) vn[l] = u[int64_t((grp % 6) * N + l) * C + ncol];
+                vn_ready = true;
+            }
+        }
+        constexpr int UR = (6 * N + LG - 1) / LG;        // coefficient rows per thread
+        constexpr int ER = (EG + LG - 1) / LG;           // element-constant rows per thread
+        constexpr int BATCH = 16;                        // loads in flight per thread
+#pragma unroll
+        for (int i0 = 0; i0 < UR; i0 += BATCH) {
+            R tmp[BATCH];
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int r = lg + (i0 + i) * LG;
+                tmp[i] = (i0 + i < UR && r < 6 * N && active) ? u[int64_t(r) * C + col] : R(0);
+            }
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int r = lg + (i0 + i) * LG;
+                if (i0 + i < UR && r < 6 * N) us[r * TE + c] = tmp[i];
+            }
+        }
+        R tmpe[ER];
+#pragma unroll
+        for (int i = 0; i < ER; ++i) {
+            const int k = lg + i * LG;
+            tmpe[i] = (k < EG && active) ? gr[int64_t(k) * K + e]
+                                         : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
+        }
+#pragma unroll
+        for (int i = 0; i < ER; ++i) {
+            const int k = lg + i * LG;
+            if (k < EG) eg[k * TE + c] = tmpe[i];
+        }
     }
-    for (int r = grp - FACE_GROUPS; r < 6 * N; r += NG - FACE_GROUPS)
-        if (r >= 0) us[r * TE + c] = active ? u[int64_t(r) * C + col] : R(0);
-    for (int k = grp; k < EG; k += NG)
-        eg[k * TE + c] = active ? gr[int64_t(k) * K + e] : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
     if (FACE_GROUPS == 0) {
         for (int f = grp; f < 4; f += NG) {
             R ait[9];
@@ -290,8 +339,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             const int64_t ne = code >> 2;
             const bool has_nbr = do_nbr && code >= 0 && ne < K;
             if (do_nbr && code >= 0 && ne >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
-            R vn[N];
-            if (has_nbr) {
+            if (has_nbr && !(rr == 0 && vn_ready)) {
                 const int64_t ncol = ne * S + s;
 #pragma unroll
                 for (int l = 0; l < N; ++l) vn[l] = u[int64_t(ncomp * N + l) * C + ncol];

@@ -117,11 +117,34 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
         face_constants2<PR>(f, ait, geo2(G_DET, 1.f), geo2(G_EPS, 1.f), geo2(G_MU, 1.f), ca, cb, gr, K,
                             prm.upwind, fg + f * FG * TE + c);
     }
-    for (int r = grp - FACE_GROUPS; r < 6 * N; r += NG - FACE_GROUPS)
-        if (r >= 0)
-            us[r * TE + c] = PR(actA ? u[int64_t(r) * C + colA] : 0.f, actB ? u[int64_t(r) * C + colB] : 0.f);
-    for (int k = grp; k < EG; k += NG)
-        eg[k * TE + c] = geo2(k, (k == G_DET || k == G_EPS || k == G_MU) ? 1.f : 0.f);
+    if (grp >= FACE_GROUPS) {
+        // all loads of a thread in flight before its first shared-memory store
+        constexpr int LG = NG - FACE_GROUPS;
+        constexpr int UR = (6 * N + LG - 1) / LG;
+        constexpr int ER = (EG + LG - 1) / LG;
+        const int lg = grp - FACE_GROUPS;
+        constexpr int BATCH = 8;
+#pragma unroll
+        for (int i0 = 0; i0 < UR; i0 += BATCH) {
+            PR tmp[BATCH];
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int r = lg + (i0 + i) * LG;
+                const bool ok = i0 + i < UR && r < 6 * N;
+                tmp[i] = PR(ok && actA ? u[int64_t(r) * C + colA] : 0.f, ok && actB ? u[int64_t(r) * C + colB] : 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int r = lg + (i0 + i) * LG;
+                if (i0 + i < UR && r < 6 * N) us[r * TE + c] = tmp[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ER; ++i) {
+            const int k = lg + i * LG;
+            if (k < EG) eg[k * TE + c] = geo2(k, (k == G_DET || k == G_EPS || k == G_MU) ? 1.f : 0.f);
+        }
+    }
     __syncthreads();
 
     // ---- phase 2: traces -------------------------------------------------------------
