@@ -133,7 +133,10 @@ def stage_bytes(K, N, S, real_size):
 
     Per stage: read u, write u_out, write res (and read res except in the first
     stage, whose coefficient a_1 = 0), plus per element the geometry record
-    (16 reals in the kernel's precision) and the neighbour table (4 int32)."""
+    (16 reals in the kernel's precision) and the neighbour table (4 int32).
+    The per-face neighbour table the kernel also reads (40 reals per element,
+    a precomputed copy of neighbour data) is not counted: it is a design
+    choice, not data the method needs, and shows up in the measured traffic."""
     field = 6 * N * K * S * real_size
     geo = K * (16 * real_size + 4 * 4)
     return (3 * field + geo) + 4 * (4 * field + geo)

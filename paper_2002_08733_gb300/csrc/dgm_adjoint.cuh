@@ -21,7 +21,8 @@
 //           (PEC: A^-1 (-2 adj(dE)_own), nothing for H), lifted with R_f^T.
 //   PML:    (F^T lam)_E -= (A^T eta A^-T)^T lam_E - eps (A^T xi A^-T)^T lam_p,
 //           (F^T lam)_p  = -lam_E / eps - (A^T Sigma A^-T)^T lam_p.
-// Gradient terms (per column, FP64), dt times:
+// Gradient terms (per column; partial sums over a work item in the kernel's
+// precision, their sum over items, stages and steps in FP64), dt times:
 //   d/d eps_T: -(1/eps) rho_E . rhs_E(T) + lam_E . p / eps^2 + lam_p . (A^T xi A^-T u_E)
 //              - Z/(2 eps) dJ/dZ_T
 //   d/d mu_T:  -(1/mu) rho_H . rhs_H(T) + lam_H . q / mu^2 + lam_q . (A^T xi A^-T u_H)
@@ -137,7 +138,7 @@ __device__ __host__ constexpr size_t adjoint_smem_bytes() {
 }
 
 template <int P, typename R, int TE, int NT>
-__global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_kernel(const AdjParams prm) {
     constexpr int N = nmodes(P);
     constexpr int NF = nfmodes(P);
     constexpr int NG = NT / TE;
@@ -165,32 +166,91 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
     const R* lam = static_cast<const R*>(prm.lr);
 
     // ---- 1: adjoint residual tile, element and face constants -------------------
-    for (int r = grp; r < 6 * N; r += NG) us[r * TE + c] = active ? lam[int64_t(r) * C + col] : R(0);
-    for (int k = grp; k < EG; k += NG)
-        eg[k * TE + c] = active ? R(prm.geo[int64_t(k) * K + e]) : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
-    for (int i = grp; i < 4 * CH; i += NG) zs[i * TE + c] = 0.0;
-    // the adjoint converts the FP64 geometry itself (FP32 copy passed as geo_r)
-    for (int i = grp; i < 2 * 6 * NPART; i += NG) gp[i * TE + c] = 0.0;
-    __syncthreads();
-    for (int f = grp; f < 4; f += NG) {
-        R ait[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
-        R* fc = fg + f * FGA * TE + c;
-        face_constants<R, TE>(f, ait, eg[G_DET * TE + c], eg[G_EPS * TE + c], eg[G_MU * TE + c],
-                              active, prm.nbr, static_cast<const R*>(prm.geo_r), K, prm.upwind, e, fc);
+    // Groups 0..3: face constants of face f = group from the element's geometry
+    // and the per-face neighbour table.  Other groups: the tile of lam and the
+    // element constants (all loads of a thread in flight before its first
+    // shared-memory store) and the neighbour lam of their first phase-2 item.
+    const R* gr = static_cast<const R*>(prm.geo_r);
+    constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
+    constexpr int LG = NG - FACE_GROUPS;
+    R vn[N];
+    bool vn_ready = false;
+    auto face_consts = [&](int f) {
+        R ait[9], aitn[9];
+        const R* fn = static_cast<const R*>(prm.fnb_r) + int64_t(f * FNB_COUNT) * K + e;
         const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
-        if (code >= 0 && (code >> 2) < K) {
-            const int64_t ne = code >> 2;
-            fc[FA_DETN * TE] = R(prm.geo[int64_t(G_DET) * K + ne]);
-            fc[FA_EPSN * TE] = R(prm.geo[int64_t(G_EPS) * K + ne]);
-            fc[FA_MUN * TE] = R(prm.geo[int64_t(G_MU) * K + ne]);
-        } else {
-            fc[FA_DETN * TE] = eg[G_DET * TE + c];
-            fc[FA_EPSN * TE] = eg[G_EPS * TE + c];
-            fc[FA_MUN * TE] = eg[G_MU * TE + c];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ait[k] = active ? gr[int64_t(G_AIT + k) * K + e] : R(k % 4 == 0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) aitn[k] = active ? fn[int64_t(FNB_AIT + k) * K] : ait[k];
+        const R det = active ? gr[int64_t(G_DET) * K + e] : R(1);
+        const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
+        const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
+        const R zn = active ? fn[int64_t(FNB_Z) * K] : R(1);
+        const bool has = code >= 0 && (code >> 2) < K;
+        R* fc = fg + f * FGA * TE + c;
+        face_constants_tab<R, TE>(f, ait, det, epsm, mum, has, aitn, zn, prm.upwind, fc);
+        fc[FA_DETN * TE] = has ? fn[int64_t(FNB_DET) * K] : det;
+        fc[FA_EPSN * TE] = has ? fn[int64_t(FNB_EPS) * K] : epsm;
+        fc[FA_MUN * TE] = has ? fn[int64_t(FNB_MU) * K] : mum;
+    };
+    if (grp < FACE_GROUPS) {
+        face_consts(grp);
+    } else {
+        const int lg = grp - FACE_GROUPS;
+        constexpr int UR = (6 * N + LG - 1) / LG;
+        constexpr int ER = (EG + LG - 1) / LG;
+        constexpr int BATCH = 16;
+        R tmp[BATCH];
+#pragma unroll
+        for (int i = 0; i < BATCH; ++i) {
+            const int r = lg + i * LG;
+            tmp[i] = (i < UR && r < 6 * N && active) ? lam[int64_t(r) * C + col] : R(0);
         }
+        if (grp < 24 && active) {   // round-0 item of phase 2: face grp / 6, component grp % 6
+            const int32_t code = prm.nbr[int64_t(grp / 6) * K + e];
+            const int64_t ne = code >> 2;
+            if (code >= 0 && ne < K) {
+                const int64_t ncol = ne * S + s;
+#pragma unroll
+                for (int l = 0; l < N; ++l) vn[l] = lam[int64_t((grp % 6) * N + l) * C + ncol];
+                vn_ready = true;
+            }
+        }
+#pragma unroll
+        for (int i0 = 0; i0 < UR; i0 += BATCH) {
+            if (i0 > 0) {
+#pragma unroll
+                for (int i = 0; i < BATCH; ++i) {
+                    const int r = lg + (i0 + i) * LG;
+                    tmp[i] = (i0 + i < UR && r < 6 * N && active) ? lam[int64_t(r) * C + col] : R(0);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int r = lg + (i0 + i) * LG;
+                if (i0 + i < UR && r < 6 * N) us[r * TE + c] = tmp[i];
+            }
+        }
+        R tmpe[ER];
+#pragma unroll
+        for (int i = 0; i < ER; ++i) {
+            const int k = lg + i * LG;
+            tmpe[i] = (k < EG && active) ? gr[int64_t(k) * K + e]
+                                         : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
+        }
+#pragma unroll
+        for (int i = 0; i < ER; ++i) {
+            const int k = lg + i * LG;
+            if (k < EG) eg[k * TE + c] = tmpe[i];
+        }
+        for (int i = lg; i < 4 * CH; i += LG) zs[i * TE + c] = 0.0;
+        for (int i = lg; i < 2 * 6 * NPART; i += LG) gp[i * TE + c] = 0.0;
     }
+    if (FACE_GROUPS == 0) {
+        for (int f = grp; f < 4; f += NG) face_consts(f);
+    }
+    __syncthreads();
     // rho = B lam per mode (field fb, rows [lo, hi))
     for (int it = grp; it < 2 * NPART; it += NG) {
         const int fb = (it / NPART) * 3;
@@ -218,8 +278,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
         const int64_t ne = code >> 2;
         const bool has_nbr = code >= 0 && ne < K;
         if (code >= 0 && ne >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
-        R vn[N];
-        if (has_nbr) {
+        if (has_nbr && !(r == grp && vn_ready)) {
             const int64_t ncol = ne * S + s;
 #pragma unroll
             for (int l = 0; l < N; ++l) vn[l] = lam[int64_t(comp * N + l) * C + ncol];
@@ -267,7 +326,7 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
         const R zp = bnd ? zm : sqrt(d[FA_MUN * TE] / d[FA_EPSN * TE]);
         const R D = (zm + zp) * (zm + zp);
         const R* jp = static_cast<const R*>(prm.jumps);
-        double zacc = 0.0;
+        R zacc = R(0);   // partial sums in the kernel's precision, FP64 from phase 6 on
         for (int m = ch * NF / CH; m < (ch + 1) * NF / CH; ++m) {
             R* own = trO + (f * 6 * NF + m) * TE + c;
             const R* nbt = trN + (f * 6 * NF + m) * TE + c;
@@ -352,27 +411,28 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
                 cross3(n, nxdE, nnxdE);
                 cross3(n, dH, nxdH);
                 cross3(n, nxdH, nnxdH);
-                double z = 0.0;
+                R z = R(0);
                 if (bnd) {
                     // Z+ = Z- = Z: d b_E/dZ = -1/(2 Z^2) on the -b_E n x (n x dE) term
+                    const R ib = R(1) / (R(2) * zm * zm);
 #pragma unroll
-                    for (int r = 0; r < 3; ++r) z += double(phiE[r]) * double(nnxdE[r]) / (2.0 * double(zm) * double(zm));
+                    for (int r = 0; r < 3; ++r) z += phiE[r] * nnxdE[r] * ib;
                 } else {
                     const R iD = R(1) / D;
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
                         // own equations (derivative in Z-)
-                        z += double(phiE[r]) * double(-zp * iD * nxdH[r] + iD * nnxdE[r]) +
-                             double(phiH[r]) * double(zp * iD * nxdE[r] + zp * zp * iD * nnxdH[r]);
+                        z += phiE[r] * (-zp * iD * nxdH[r] + iD * nnxdE[r]) +
+                             phiH[r] * (zp * iD * nxdE[r] + zp * zp * iD * nnxdH[r]);
                         // neighbour's equations (derivative in its Z+ = this element's Z)
-                        z += double(phiEn[r]) * double(zp * iD * nxdH[r] - iD * nnxdE[r]) +
-                             double(phiHn[r]) * double(-zp * iD * nxdE[r] - zp * zp * iD * nnxdH[r]);
+                        z += phiEn[r] * (zp * iD * nxdH[r] - iD * nnxdE[r]) +
+                             phiHn[r] * (-zp * iD * nxdE[r] - zp * zp * iD * nnxdH[r]);
                     }
                 }
                 zacc += z;
             }
         }
-        zs[it * TE + c] = zacc;
+        zs[it * TE + c] = double(zacc);
     }
     __syncthreads();
 
@@ -438,13 +498,13 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
         const R* af = static_cast<const R*>(prm.aux);
         const R* raw = static_cast<const R*>(prm.raw);
         const R dt = R(prm.dt);
-        double gmass = 0.0, gpml = 0.0;
+        R gmass = R(0), gpml = R(0);   // partial sums in the kernel's precision
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
         for (int l = lo; l < hi; ++l) {
             R w = rh[(comp * N + l) * TE + c];
             const int64_t gi = int64_t(comp * N + l) * C + col;
             // mass term of the gradient: -(1/mat) rho_c . rhs_c
-            gmass += double(rs[(comp * N + l) * TE + c]) * double(raw[gi]);
+            gmass += rs[(comp * N + l) * TE + c] * raw[gi];
             if (pi >= 0) {
                 const R l0 = us[((fb + 0) * N + l) * TE + c];
                 const R l1 = us[((fb + 1) * N + l) * TE + c];
@@ -463,13 +523,12 @@ __global__ void __launch_bounds__(NT, 1) adjoint_kernel(const AdjParams prm) {
                 const R u0 = uf[int64_t((fb + 0) * N + l) * C + col];
                 const R u1 = uf[int64_t((fb + 1) * N + l) * C + col];
                 const R u2 = uf[int64_t((fb + 2) * N + l) * C + col];
-                gpml += double(lj) * double(apj) / (double(mat) * double(mat)) +
-                        double(pj) * double(xiR[0] * u0 + xiR[1] * u1 + xiR[2] * u2);
+                gpml += lj * apj / (mat * mat) + pj * (xiR[0] * u0 + xiR[1] * u1 + xiR[2] * u2);
             }
             lu[gi] += dt * w;
         }
         const int slot = comp < 3 ? 0 : 1;
-        gp[(slot * 6 * NPART + it) * TE + c] = -gmass / double(mat) + gpml;
+        gp[(slot * 6 * NPART + it) * TE + c] = double(-gmass / mat + gpml);
     }
     __syncthreads();
 

@@ -65,7 +65,7 @@ struct dgm_plan {
     bool has_pml = false;
     // geometry buffer layout (byte offsets)
     size_t off_geo = 0, off_nbr = 0, off_pml = 0, off_src = 0, off_part = 0, off_status = 0,
-           off_rec = 0, off_time = 0, off_geo32 = 0, bytes_geom = 0;
+           off_rec = 0, off_time = 0, off_geo32 = 0, off_fnb = 0, off_fnb32 = 0, bytes_geom = 0;
     int n_rec = 0;
     std::vector<double> src_host;   // S * (SRC_HDR + 3N)
     bool have_src = false;
@@ -231,6 +231,10 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
     off = align256(off + sizeof(double) * G_COUNT * K);
     P->off_geo32 = off;   // FP32 copy of the geometry for FP32 kernels
     off = align256(off + sizeof(float) * G_COUNT * K);
+    P->off_fnb = off;     // per-face neighbour table, FP64 and FP32
+    off = align256(off + sizeof(double) * 4 * FNB_COUNT * K);
+    P->off_fnb32 = off;
+    off = align256(off + sizeof(float) * 4 * FNB_COUNT * K);
     P->off_nbr = off;
     off = align256(off + sizeof(int32_t) * 4 * K);
     P->off_pml = off;
@@ -272,6 +276,43 @@ int dgm_plan_info(const dgm_plan* P, dgm_info* out) {
     out->bytes_geom = P->bytes_geom;
     out->n_quad = (P->opt.p + 3) * (P->opt.p + 3) * (P->opt.p + 3);
     return DGM_OK;
+}
+
+// Per-face neighbour table (FnbSlot) from the FP64 geometry, in FP64 and FP32.
+__global__ void face_table_kernel(const double* __restrict__ geo, const int32_t* __restrict__ nbr,
+                                  int64_t K, double* __restrict__ t64, float* __restrict__ t32) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= 4 * K) return;
+    const int f = int(i / K);
+    const int64_t e = i - int64_t(f) * K;
+    const int32_t code = nbr[i];
+    const int64_t src = (code >= 0 && (code >> 2) < K) ? int64_t(code >> 2) : e;
+    for (int k = 0; k < 9; ++k) {
+        const double v = geo[int64_t(G_AIT + k) * K + src];
+        t64[int64_t(f * FNB_COUNT + FNB_AIT + k) * K + e] = v;
+        t32[int64_t(f * FNB_COUNT + FNB_AIT + k) * K + e] = float(v);
+    }
+    const double z = sqrt(geo[int64_t(G_MU) * K + src] / geo[int64_t(G_EPS) * K + src]);
+    t64[int64_t(f * FNB_COUNT + FNB_Z) * K + e] = z;
+    t32[int64_t(f * FNB_COUNT + FNB_Z) * K + e] = float(z);
+    const int gs[3] = {G_DET, G_EPS, G_MU};
+    for (int k = 0; k < 3; ++k) {
+        const double v = geo[int64_t(gs[k]) * K + src];
+        t64[int64_t(f * FNB_COUNT + FNB_DET + k) * K + e] = v;
+        t32[int64_t(f * FNB_COUNT + FNB_DET + k) * K + e] = float(v);
+    }
+}
+
+static int build_face_table(dgm_plan* P) {
+    const int64_t K = P->mesh.K;
+    if (K == 0) return DGM_OK;
+    const unsigned grid = unsigned((4 * K + 255) / 256);
+    face_table_kernel<<<grid, 256, 0, P->stream>>>(
+        reinterpret_cast<const double*>(P->geom + P->off_geo),
+        reinterpret_cast<const int32_t*>(P->geom + P->off_nbr), K,
+        reinterpret_cast<double*>(P->geom + P->off_fnb), reinterpret_cast<float*>(P->geom + P->off_fnb32));
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "face table");
 }
 
 int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, void* aux0,
@@ -317,6 +358,7 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
         return cuda_fail(e, "upload sources");
     if ((e = cudaMemsetAsync(P->geom + P->off_status, 0, 64, st)) != cudaSuccess)
         return cuda_fail(e, "clear status");
+    if (int rc = build_face_table(P)) return rc;
     // the host copies above are pageable: finish them before the host vectors can change
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
     P->bound = true;
@@ -329,6 +371,8 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.geo_r = P->kt->real_size == 8 ? static_cast<const void*>(P->geom + P->off_geo)
                                       : static_cast<const void*>(P->geom + P->off_geo32);
     prm.nbr = reinterpret_cast<const int32_t*>(P->geom + P->off_nbr);
+    prm.fnb_r = P->kt->real_size == 8 ? static_cast<const void*>(P->geom + P->off_fnb)
+                                      : static_cast<const void*>(P->geom + P->off_fnb32);
     prm.pml = P->has_pml ? reinterpret_cast<const int32_t*>(P->geom + P->off_pml) : nullptr;
     prm.src = P->have_src ? reinterpret_cast<const double*>(P->geom + P->off_src) : nullptr;
     prm.status = reinterpret_cast<int32_t*>(P->geom + P->off_status);
@@ -967,6 +1011,7 @@ extern "C" int dgm_set_materials(dgm_plan* P, const double* eps, const double* m
     e = cudaMemcpyAsync(P->geom + P->off_geo32 + sizeof(float) * G_EPS * K, m32.data(),
                         sizeof(float) * 2 * K, cudaMemcpyHostToDevice, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "upload materials (FP32)");
+    if (int rc = build_face_table(P)) return rc;
     if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "materials sync");
     return DGM_OK;
 }
@@ -1116,6 +1161,7 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
                 ap.jumps = ws + L.jmp;
                 ap.geo = prm.geo;
                 ap.geo_r = prm.geo_r;
+                ap.fnb_r = prm.fnb_r;
                 ap.nbr = prm.nbr;
                 ap.pml = prm.pml;
                 ap.status = prm.status;

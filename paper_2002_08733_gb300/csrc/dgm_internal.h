@@ -27,6 +27,14 @@ enum GeoSlot {
     G_COUNT = 16
 };
 
+// Per-face neighbour table (rebuilt on the device whenever geometry or
+// materials change): for face f of element e, slot f * FNB_COUNT + k holds
+// the neighbour's A^-T (k = 0..8, row major), its impedance sqrt(mu/eps)
+// (k = 9), det A, eps and mu (k = 10..12); on a boundary face the element's
+// own values.  It turns the neighbour-geometry gathers of the face constants
+// into coalesced reads (the stage kernel reads k = 0..9, the adjoint all).
+enum FnbSlot { FNB_AIT = 0, FNB_Z = 9, FNB_DET = 10, FNB_EPS = 11, FNB_MU = 12, FNB_COUNT = 13 };
+
 // Source record per column (FP64): [elem, f0, bw, t0, 0,0,0,0, w[3N]].
 constexpr int SRC_HDR = 8;
 
@@ -44,6 +52,7 @@ struct StageParams {
     const double* geo;    // [G_COUNT][K] FP64 master copy
     const void* geo_r;    // the same in the kernel's real type (FP32 copy for FP32 kernels)
     const int32_t* nbr;   // [4][K]: (neighbour << 2) | neighbour's local face, or -1
+    const void* fnb_r;    // [4][FNB_COUNT][K] per-face neighbour data in the kernel's real type
     const int32_t* pml;   // [K]: index into aux, or -1 (may be null without PML)
     const double* src;    // [S][SRC_HDR + 3N] or null
     int32_t* status;      // device status word
@@ -71,6 +80,7 @@ struct AdjParams {
     const void* jumps;    // forward physical face jumps
     const double* geo;
     const void* geo_r;    // geometry in the kernel's real type
+    const void* fnb_r;    // per-face neighbour table in the kernel's real type
     const int32_t* nbr;
     const int32_t* pml;
     int32_t* status;

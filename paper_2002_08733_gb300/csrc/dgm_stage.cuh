@@ -158,6 +158,42 @@ __device__ __forceinline__ void face_constants(int f, const R (&ait)[9], R det, 
     }
 }
 
+// The same face constants from the per-face neighbour table (neighbour's
+// A^-T and impedance, own values on a boundary face) instead of a gather of
+// the neighbour's geometry: every input is one coalesced load.
+template <typename R, int TE>
+__device__ __forceinline__ void face_constants_tab(int f, const R (&ait)[9], R det, R epsm, R mum,
+                                                   bool has_nbr, const R (&aitn)[9], R zn,
+                                                   int upwind, R* fc) {
+    const R m0 = R(f == 0 ? 1 : (f == 1 ? -1 : 0));
+    const R m1 = R(f == 0 ? 1 : (f == 2 ? -1 : 0));
+    const R m2 = R(f == 0 ? 1 : (f == 3 ? -1 : 0));
+    R vn[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) vn[r] = ait[3 * r + 0] * m0 + ait[3 * r + 1] * m1 + ait[3 * r + 2] * m2;
+    const R fs = sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) fc[(FC_N + r) * TE] = vn[r] / fs;
+    fc[FC_TWOF * TE] = fabs(det) * fs;
+    const R zm = sqrt(mum / epsm);
+    const R zp = has_nbr ? zn : zm;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = aitn[k];
+    fc[FC_BND * TE] = has_nbr ? R(0) : R(1);
+    if (upwind) {
+        const R ym = R(1) / zm, yp = R(1) / zp;
+        fc[FC_CE * TE] = zp / (zm + zp);
+        fc[FC_BE * TE] = R(1) / (zm + zp);
+        fc[FC_CH * TE] = yp / (ym + yp);
+        fc[FC_BH * TE] = R(1) / (ym + yp);
+    } else {
+        fc[FC_CE * TE] = R(0.5);
+        fc[FC_BE * TE] = R(0);
+        fc[FC_CH * TE] = R(0.5);
+        fc[FC_BH * TE] = R(0);
+    }
+}
+
 // Right-hand side rows [LO, HI) of component `comp` (before the mass inverse):
 // volume curl of the other field plus the lift of the pulled-back fluxes.
 template <int P, typename R, int TE, int LO, int HI>
@@ -238,13 +274,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     if (grp < 4) nbs[grp * TE + c] = active ? prm.nbr[int64_t(grp) * K + e] : -1;
 
     // ---- phase 1: tile coefficients, element and face constants --------------
-    // Groups 0..3 compute the face constants of face f = group straight from
-    // global memory (two dependent round trips: neighbour code, then the
-    // neighbour's geometry).  The other groups stage the tile's coefficients
-    // and element constants, each thread issuing all its loads before its
-    // first shared-memory store, and request the neighbour coefficients of
-    // their first phase-2 item, so that every global round trip of the tile
-    // is in flight at once.
+    // Groups 0..3 compute the face constants of face f = group from the
+    // element's geometry and the per-face neighbour table (one round trip).
+    // The other groups stage the tile's coefficients and element constants,
+    // each thread issuing its loads before its first shared-memory store, and
+    // request the neighbour coefficients of their first phase-2 item, so that
+    // the global round trips of the tile overlap.
     constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
     constexpr int LG = NG - FACE_GROUPS;                 // loading groups
     R vn[N];                                            // neighbour coefficients (phase 2)
@@ -252,18 +287,36 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     auto nbr_item_active = [&](int comp) {
         return !((MODE == MODE_LF_E && comp < 3) || (MODE == MODE_LF_H && comp >= 3));
     };
-    if (grp < FACE_GROUPS) {
-        const int f = grp;
-        R ait[9];
+    auto face_consts = [&](int f) {
+        R ait[9], aitn[9];
+        const R* fn = static_cast<const R*>(prm.fnb_r) + int64_t(f * FNB_COUNT) * K + e;
+        const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
 #pragma unroll
         for (int k = 0; k < 9; ++k) ait[k] = active ? gr[int64_t(G_AIT + k) * K + e] : R(k % 4 == 0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) aitn[k] = active ? fn[int64_t(FNB_AIT + k) * K] : ait[k];
         const R det = active ? gr[int64_t(G_DET) * K + e] : R(1);
         const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
         const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
-        face_constants<R, TE>(f, ait, det, epsm, mum, active, prm.nbr, gr, K, prm.upwind, e, fg + f * FG * TE + c);
+        const R zn = active ? fn[int64_t(FNB_Z) * K] : R(1);
+        face_constants_tab<R, TE>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
+                                  prm.upwind, fg + f * FG * TE + c);
+    };
+    if (grp < FACE_GROUPS) {
+        face_consts(grp);
     } else {
         const int lg = grp - FACE_GROUPS;
-        // round-0 neighbour item of this group: face ni / 6, component ni % 6
+        constexpr int UR = (6 * N + LG - 1) / LG;        // coefficient rows per thread
+        constexpr int ER = (EG + LG - 1) / LG;           // element-constant rows per thread
+        constexpr int BATCH = 16;                        // loads in flight per thread
+        // first batch of tile rows and the round-0 neighbour code in flight together
+        R tmp[BATCH];
+#pragma unroll
+        for (int i = 0; i < BATCH; ++i) {
+            const int r = lg + i * LG;
+            tmp[i] = (i < UR && r < 6 * N && active) ? u[int64_t(r) * C + col] : R(0);
+        }
+        // round-0 neighbour item of this group: face grp / 6, component grp % 6
         if (grp < 24 && nbr_item_active(grp % 6) && active) {
             const int32_t code = prm.nbr[int64_t(grp / 6) * K + e];
             const int64_t ne = code >> 2;
@@ -274,16 +327,14 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
                 vn_ready = true;
             }
         }
-        constexpr int UR = (6 * N + LG - 1) / LG;        // coefficient rows per thread
-        constexpr int ER = (EG + LG - 1) / LG;           // element-constant rows per thread
-        constexpr int BATCH = 16;                        // loads in flight per thread
 #pragma unroll
         for (int i0 = 0; i0 < UR; i0 += BATCH) {
-            R tmp[BATCH];
+            if (i0 > 0) {
 #pragma unroll
-            for (int i = 0; i < BATCH; ++i) {
-                const int r = lg + (i0 + i) * LG;
-                tmp[i] = (i0 + i < UR && r < 6 * N && active) ? u[int64_t(r) * C + col] : R(0);
+                for (int i = 0; i < BATCH; ++i) {
+                    const int r = lg + (i0 + i) * LG;
+                    tmp[i] = (i0 + i < UR && r < 6 * N && active) ? u[int64_t(r) * C + col] : R(0);
+                }
             }
 #pragma unroll
             for (int i = 0; i < BATCH; ++i) {
@@ -305,15 +356,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         }
     }
     if (FACE_GROUPS == 0) {
-        for (int f = grp; f < 4; f += NG) {
-            R ait[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) ait[k] = active ? gr[int64_t(G_AIT + k) * K + e] : R(k % 4 == 0);
-            const R det = active ? gr[int64_t(G_DET) * K + e] : R(1);
-            const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
-            const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
-            face_constants<R, TE>(f, ait, det, epsm, mum, active, prm.nbr, gr, K, prm.upwind, e, fg + f * FG * TE + c);
-        }
+        for (int f = grp; f < 4; f += NG) face_consts(f);
     }
     __syncthreads();
 

@@ -16,9 +16,8 @@ namespace dgm {
 
 template <typename PR>
 __device__ __forceinline__ void face_constants2(int f, const PR (&ait)[9], PR det, PR epsm, PR mum,
-                                                const int32_t codeA, const int32_t codeB,
-                                                const float* __restrict__ gr, int64_t K, int upwind,
-                                                PR* fc) {
+                                                bool hA, bool hB, const PR (&aitn)[9], PR zn,
+                                                int upwind, PR* fc) {
     constexpr int TE = 32;
     const PR m0 = PR(f == 0 ? 1.0 : (f == 1 ? -1.0 : 0.0));
     const PR m1 = PR(f == 0 ? 1.0 : (f == 2 ? -1.0 : 0.0));
@@ -32,17 +31,9 @@ __device__ __forceinline__ void face_constants2(int f, const PR (&ait)[9], PR de
     for (int r = 0; r < 3; ++r) fc[(FC_N + r) * TE] = vn[r] * ifs;
     fc[FC_TWOF * TE] = pabs(det) * fs;
     const PR zm = psqrt(mum * prcp(epsm));
-    const bool hA = codeA >= 0 && (codeA >> 2) < K, hB = codeB >= 0 && (codeB >> 2) < K;
-    const int64_t nA = hA ? (codeA >> 2) : 0, nB = hB ? (codeB >> 2) : 0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const float a = hA ? gr[int64_t(G_AIT + k) * K + nA] : ait[k].a();
-        const float b = hB ? gr[int64_t(G_AIT + k) * K + nB] : ait[k].b();
-        fc[(FC_AITN + k) * TE] = PR(a, b);
-    }
-    const float zpa = hA ? sqrtf(gr[int64_t(G_MU) * K + nA] / gr[int64_t(G_EPS) * K + nA]) : zm.a();
-    const float zpb = hB ? sqrtf(gr[int64_t(G_MU) * K + nB] / gr[int64_t(G_EPS) * K + nB]) : zm.b();
-    const PR zp(zpa, zpb);
+    for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = aitn[k];
+    const PR zp = psel(hA, hB, zn, zm);
     fc[FC_BND * TE] = PR(hA ? 0.f : 1.f, hB ? 0.f : 1.f);
     if (upwind) {
         const PR isum = prcp(zm + zp);
@@ -109,13 +100,20 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
     constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
     if (grp < FACE_GROUPS) {
         const int f = grp;
-        PR ait[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) ait[k] = geo2(G_AIT + k, k % 4 == 0 ? 1.f : 0.f);
+        const float* fn = static_cast<const float*>(prm.fnb_r) + int64_t(f * FNB_COUNT) * K;
         const int32_t ca = actA ? prm.nbr[int64_t(f) * K + eA] : -1;
         const int32_t cb = actB ? prm.nbr[int64_t(f) * K + eB] : -1;
-        face_constants2<PR>(f, ait, geo2(G_DET, 1.f), geo2(G_EPS, 1.f), geo2(G_MU, 1.f), ca, cb, gr, K,
-                            prm.upwind, fg + f * FG * TE + c);
+        PR ait[9], aitn[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ait[k] = geo2(G_AIT + k, k % 4 == 0 ? 1.f : 0.f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            aitn[k] = PR(actA ? fn[int64_t(FNB_AIT + k) * K + eA] : ait[k].a(),
+                         actB ? fn[int64_t(FNB_AIT + k) * K + eB] : ait[k].b());
+        const PR zn(actA ? fn[int64_t(FNB_Z) * K + eA] : 1.f, actB ? fn[int64_t(FNB_Z) * K + eB] : 1.f);
+        face_constants2<PR>(f, ait, geo2(G_DET, 1.f), geo2(G_EPS, 1.f), geo2(G_MU, 1.f),
+                            ca >= 0 && (ca >> 2) < K, cb >= 0 && (cb >> 2) < K, aitn, zn, prm.upwind,
+                            fg + f * FG * TE + c);
     }
     if (grp >= FACE_GROUPS) {
         // all loads of a thread in flight before its first shared-memory store

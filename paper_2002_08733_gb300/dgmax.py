@@ -396,12 +396,16 @@ def receiver_records(solver, eps, mu, n_steps, t0=0.0, u0=None, aux0=None):
         @staticmethod
         def forward(ctx, e, m):
             solver.set_materials(e.detach().cpu().numpy(), m.detach().cpu().numpy())
-            K, S, N = solver.K, solver.S, solver.N
-            solver.set_state(np.zeros((K, S, 6, N)) if u0 is None else u0)
+            if u0 is None:   # start from rest without a host round trip
+                solver.torch.cuda.synchronize(solver.device)
+                solver.fields[solver.current()].zero_()
+            else:
+                solver.set_state(u0)
             if solver.npml:
                 solver.aux[solver.current()].zero_()
                 if aux0 is not None:
                     solver.aux[solver.current()].copy_(solver.aux_to_device(aux0))
+            solver.torch.cuda.synchronize(solver.device)   # fills above ran on torch's stream
             ws = solver.adjoint_workspace(n_steps)
             rec = solver.forward_record(n_steps, t0, ws)
             ctx.ws = ws
