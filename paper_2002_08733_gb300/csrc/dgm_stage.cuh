@@ -277,15 +277,24 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     // Groups 0..3 compute the face constants of face f = group from the
     // element's geometry and the per-face neighbour table (one round trip).
     // The other groups stage the tile's coefficients and element constants,
-    // each thread issuing its loads before its first shared-memory store, and
-    // request the neighbour coefficients of their first phase-2 item, so that
-    // the global round trips of the tile overlap.
+    // each thread issuing its loads before its first shared-memory store.
+    // Every group requests the neighbour coefficients of its first phase-2
+    // item, so that the global round trips of the tile overlap.
     constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
     constexpr int LG = NG - FACE_GROUPS;                 // loading groups
+    constexpr int NOWN = 12, NNBR = 24;                 // phase-2 items
     R vn[N];                                            // neighbour coefficients (phase 2)
-    bool vn_ready = false;                              // round-0 item prefetched in phase 1
     auto nbr_item_active = [&](int comp) {
         return !((MODE == MODE_LF_E && comp < 3) || (MODE == MODE_LF_H && comp >= 3));
+    };
+    // neighbour item ni = (face ni / 6, component ni % 6): request the
+    // neighbour's coefficients of that component given the face's code
+    auto request_nbr = [&](int ni, int32_t code, R (&dst)[N]) {
+        if (ni < NNBR && nbr_item_active(ni % 6) && active && code >= 0 && (code >> 2) < K) {
+            const int64_t ncol = int64_t(code >> 2) * S + s;
+#pragma unroll
+            for (int l = 0; l < N; ++l) dst[l] = u[int64_t((ni % 6) * N + l) * C + ncol];
+        }
     };
     auto face_consts = [&](int f) {
         R ait[9], aitn[9];
@@ -302,31 +311,32 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         face_constants_tab<R, TE>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
                                   prm.upwind, fg + f * FG * TE + c);
     };
+    // neighbour code of this group's round-0 item, loaded with the other
+    // independent loads so that the dependent gather starts one round trip in
+    const int32_t code0 = (grp < NNBR && active) ? prm.nbr[int64_t(grp / 6) * K + e] : -1;
     if (grp < FACE_GROUPS) {
         face_consts(grp);
+        request_nbr(grp, code0, vn);
     } else {
         const int lg = grp - FACE_GROUPS;
         constexpr int UR = (6 * N + LG - 1) / LG;        // coefficient rows per thread
         constexpr int ER = (EG + LG - 1) / LG;           // element-constant rows per thread
         constexpr int BATCH = 16;                        // loads in flight per thread
-        // first batch of tile rows and the round-0 neighbour code in flight together
+        // first batch of tile rows, element constants and the round-0 code in flight together
         R tmp[BATCH];
 #pragma unroll
         for (int i = 0; i < BATCH; ++i) {
             const int r = lg + i * LG;
             tmp[i] = (i < UR && r < 6 * N && active) ? u[int64_t(r) * C + col] : R(0);
         }
-        // round-0 neighbour item of this group: face grp / 6, component grp % 6
-        if (grp < 24 && nbr_item_active(grp % 6) && active) {
-            const int32_t code = prm.nbr[int64_t(grp / 6) * K + e];
-            const int64_t ne = code >> 2;
-            if (code >= 0 && ne < K) {
-                const int64_t ncol = ne * S + s;
+        R tmpe[ER];
 #pragma unroll
-                for (int l = 0; l < N; ++l) vn[l] = u[int64_t((grp % 6) * N + l) * C + ncol];
-                vn_ready = true;
-            }
+        for (int i = 0; i < ER; ++i) {
+            const int k = lg + i * LG;
+            tmpe[i] = (k < EG && active) ? gr[int64_t(k) * K + e]
+                                         : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
         }
+        request_nbr(grp, code0, vn);
 #pragma unroll
         for (int i0 = 0; i0 < UR; i0 += BATCH) {
             if (i0 > 0) {
@@ -342,13 +352,6 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
                 if (i0 + i < UR && r < 6 * N) us[r * TE + c] = tmp[i];
             }
         }
-        R tmpe[ER];
-#pragma unroll
-        for (int i = 0; i < ER; ++i) {
-            const int k = lg + i * LG;
-            tmpe[i] = (k < EG && active) ? gr[int64_t(k) * K + e]
-                                         : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
-        }
 #pragma unroll
         for (int i = 0; i < ER; ++i) {
             const int k = lg + i * LG;
@@ -361,54 +364,25 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     __syncthreads();
 
     // ---- phase 2: traces ------------------------------------------------------
-    // Own traces: item (component, pair of faces) shares one load of the
-    // component's coefficients between two faces.  Neighbour traces: item
-    // (face, component); the neighbour's coefficients are requested before the
-    // own-trace arithmetic so that their latency overlaps it.
+    // Neighbour traces: item (face, component), one per group and round; the
+    // coefficients of round rr + 1 are requested before the arithmetic of
+    // round rr (those of round 0 in phase 1), so every gather overlaps work.
+    // Own traces: item (component, pair of faces), sharing one load of the
+    // component's coefficients between two faces, in the last rounds.
     {
-        constexpr int NOWN = 12, NNBR = 24;
         constexpr int ROUNDS = (NNBR + NG - 1) / NG;
+        constexpr int OWN_ROUNDS = (NOWN + NG - 1) / NG;
 #pragma unroll 1
         for (int rr = 0; rr < ROUNDS; ++rr) {
-            const int ni = grp + rr * NG;           // neighbour item
-            const int oi = ni;                      // own item handled in the same round
-            // neighbour item: face f, component comp
-            bool do_nbr = ni < NNBR;
-            const int nf = ni / 6, ncomp = ni % 6;
-            if (MODE == MODE_LF_E && ncomp < 3) do_nbr = false;
-            if (MODE == MODE_LF_H && ncomp >= 3) do_nbr = false;
-            int32_t code = -1;
-            if (do_nbr) code = nbs[nf * TE + c];
-            const int64_t ne = code >> 2;
-            const bool has_nbr = do_nbr && code >= 0 && ne < K;
-            if (do_nbr && code >= 0 && ne >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
-            if (has_nbr && !(rr == 0 && vn_ready)) {
-                const int64_t ncol = ne * S + s;
-#pragma unroll
-                for (int l = 0; l < N; ++l) vn[l] = u[int64_t(ncomp * N + l) * C + ncol];
-            }
-            // own item: component ocomp, faces 2*fp and 2*fp+1
-            if (oi < NOWN) {
-                const int ocomp = oi % 6, fp = oi / 6;
-                bool do_own = true;
-                if (MODE == MODE_LF_E && ocomp < 3) do_own = false;
-                if (MODE == MODE_LF_H && ocomp >= 3) do_own = false;
-                if (do_own) {
-                    R v[N];
-                    R acc[NF];
-#pragma unroll
-                    for (int l = 0; l < N; ++l) v[l] = us[(ocomp * N + l) * TE + c];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int f = 2 * fp + h;
-                        trace_any<P, R>(f, v, acc);
-                        R* dst = trO + ((f * 6 + ocomp) * NF) * TE + c;
-#pragma unroll
-                        for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
-                    }
-                }
-            }
-            if (do_nbr) {
+            const int ni = grp + rr * NG;
+            R vnx[N];
+            if (rr + 1 < ROUNDS && ni + NG < NNBR)
+                request_nbr(ni + NG, nbs[((ni + NG) / 6) * TE + c], vnx);
+            if (ni < NNBR && nbr_item_active(ni % 6)) {
+                const int nf = ni / 6, ncomp = ni % 6;
+                const int32_t code = nbs[nf * TE + c];
+                const bool has_nbr = code >= 0 && (code >> 2) < K;
+                if (code >= 0 && (code >> 2) >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
                 R acc[NF];
                 if (has_nbr) {
                     trace_any<P, R>(code & 3, vn, acc);
@@ -420,6 +394,24 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
 #pragma unroll
                 for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
             }
+            const int oi = grp + (rr - (ROUNDS - OWN_ROUNDS)) * NG;   // own item of this round
+            if (rr >= ROUNDS - OWN_ROUNDS && oi < NOWN && nbr_item_active(oi % 6)) {
+                const int ocomp = oi % 6, fp = oi / 6;
+                R v[N];
+                R acc[NF];
+#pragma unroll
+                for (int l = 0; l < N; ++l) v[l] = us[(ocomp * N + l) * TE + c];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int f = 2 * fp + h;
+                    trace_any<P, R>(f, v, acc);
+                    R* dst = trO + ((f * 6 + ocomp) * NF) * TE + c;
+#pragma unroll
+                    for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < N; ++l) vn[l] = vnx[l];
         }
     }
     __syncthreads();

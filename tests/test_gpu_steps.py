@@ -43,6 +43,31 @@ def test_lsrk4_trajectory(D, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_lsrk4_tile_load_paths(D, prec, tol, S):
+    """Both ways the stage kernel stages its tile: bulk asynchronous copies
+    when a row of C = 162 S columns is a multiple of 16 bytes (FP32: S = 2;
+    FP64: every S) and per-thread loads otherwise (FP32: S = 1, 3), with PML
+    auxiliaries and a source in column 0."""
+    xyz, tets = W.kuhn_mesh(3, (-1, -1, -1), (1, 1, 1), jitter=0.1, seed=23)
+    K, p = len(tets), 2
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+    srcs = [W.dipole((0.11, -0.07, 0.05), 2.0, 1.0)] + [None] * (S - 1)
+    dt = W.stable_dt(2 / 3, p)
+    u = W.random_state(K, S, p, seed=24) * 1e-2
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", dt, S=S, pml=pml)
+    g.set_sources(srcs)
+    g.set_state(u)
+    g.advance(6, 0.0)
+    got = g.state()
+    o = build(xyz, tets, p, 1.0, 1.0, "upwind", pml=pml, S=S, sources=srcs)
+    ref, ref_aux = o.unpack(o.lsrk4(o.pack(u, np.zeros_like(u)), 0.0, dt, 6))
+    assert rel_l2(got, ref) < tol
+    ga = g.from_device(g.aux[g.current()])
+    assert rel_l2(ga, ref_aux[g.pml_elements()]) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_lsrk4_pml_dipole_trajectory(D, prec, tol):
     xyz, tets = W.kuhn_mesh(4, (-1, -1, -1), (1, 1, 1))
     K, p, S = len(tets), 2, 1
