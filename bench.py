@@ -343,6 +343,8 @@ def run_adjoint(steps):
         target = D.receiver_records(g, torch.tensor(w.extra["eps_target"]), mu, steps)
     eps = torch.tensor(w.extra["eps"], requires_grad=True)
     mu_p = mu.clone().requires_grad_(True)
+    # warm the PyTorch kernels of the loss (their first call loads or JIT-compiles them)
+    float((0.5 * ((target - target) ** 2).sum()).item())
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     r = D.receiver_records(g, eps, mu_p, steps)

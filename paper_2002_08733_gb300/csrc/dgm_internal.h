@@ -61,6 +61,7 @@ struct StageParams {
     int32_t S;
     int32_t upwind;
     double t, dt, a, b;   // stage time, step, LSRK coefficients a_k, b_k
+    float dt_f, a_f, b_f; // the same rounded to FP32 (set by the launchers for FP32 kernels)
     const double* tdev;   // if set: stage time = *tdev + t (device clock of graph replays)
     void* raw;            // MODE_RAW: right-hand side before the mass inverse [6][N][K][S]
     void* jumps;          // MODE_RAW: physical face jumps dE, dH [4][6][NF][K][S]

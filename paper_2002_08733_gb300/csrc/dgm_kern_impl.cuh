@@ -68,7 +68,11 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     const int64_t C = prm.K * prm.S;
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + 63) / 64);
-    k<<<grid, kNT, smem, st>>>(prm);
+    StageParams q = prm;
+    q.dt_f = float(prm.dt);
+    q.a_f = float(prm.a);
+    q.b_f = float(prm.b);
+    k<<<grid, kNT, smem, st>>>(q);
     return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
 }
 #else
@@ -85,7 +89,11 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     const int64_t C = prm.K * prm.S;
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + kTE - 1) / kTE);
-    k<<<grid, kNT, smem, st>>>(prm);
+    StageParams q = prm;
+    q.dt_f = float(prm.dt);
+    q.a_f = float(prm.a);
+    q.b_f = float(prm.b);
+    k<<<grid, kNT, smem, st>>>(q);
     return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
 }
 #endif

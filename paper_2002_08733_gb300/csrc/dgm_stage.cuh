@@ -511,7 +511,10 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     constexpr int RPF = (N + NPART - 1) / NPART;
     constexpr bool PREFETCH_RES = (MODE == MODE_LSRK) && (6 * NPART <= NG);
     R resv[PREFETCH_RES ? RPF : 1];
-    if (PREFETCH_RES && grp < 6 * NPART && active && prm.a != 0.0) {
+    // stage coefficients in the kernel's precision: FP32 kernels read the FP32
+    // copies, so that no conversion runs on the FP64 pipe
+    auto coef = [&](double d, float f) { return sizeof(R) == 4 ? R(f) : R(d); };
+    if (PREFETCH_RES && grp < 6 * NPART && active && coef(prm.a, prm.a_f) != R(0)) {
         const int comp = grp / NPART, part = grp % NPART;
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
         const R* __restrict__ res = static_cast<const R*>(prm.res);
@@ -617,7 +620,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         const R* __restrict__ aux = static_cast<const R*>(prm.aux);
         R* __restrict__ auxo = static_cast<R*>(prm.aux_out);
         R* __restrict__ auxr = static_cast<R*>(prm.aux_res);
-        const R dt = R(prm.dt), ca = R(prm.a), cb = R(prm.b);
+        const R dt = coef(prm.dt, prm.dt_f), ca = coef(prm.a, prm.a_f), cb = coef(prm.b, prm.b_f);
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
         // rows l = lo + i with a compile-time i, so that the prefetched
         // residuals stay in registers

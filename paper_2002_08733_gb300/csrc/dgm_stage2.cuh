@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
     constexpr bool PREFETCH_RES = 6 * NPART <= NG;
     PR resv[PREFETCH_RES ? RPF : 1];
     const float* resg = static_cast<const float*>(prm.res);
-    if (PREFETCH_RES && grp < 6 * NPART && prm.a != 0.0) {
+    if (PREFETCH_RES && grp < 6 * NPART && prm.a_f != 0.f) {
         const int comp = grp / NPART, part = grp % NPART;
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
 #pragma unroll
@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
         const float* aux = static_cast<const float*>(prm.aux);
         float* auxo = static_cast<float*>(prm.aux_out);
         float* auxr = static_cast<float*>(prm.aux_res);
-        const PR dt = PR(prm.dt), cb = PR(prm.b);
-        const float ca = float(prm.a);
+        const PR dt = PR(prm.dt_f, prm.dt_f), cb = PR(prm.b_f, prm.b_f);
+        const float ca = prm.a_f;
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
 #pragma unroll
         for (int i = 0; i < RPF; ++i) {
@@ -414,14 +414,14 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
                               (sig_row[0] * a0 + sig_row[1] * a1 + sig_row[2] * a2);
                 const int64_t rw = int64_t(comp * N + l) * C2;
                 if (piA >= 0) {
-                    const float rr = (ca == 0.f ? 0.f : ca * auxr[rw + acA]) + float(prm.dt) * da.a();
+                    const float rr = (ca == 0.f ? 0.f : ca * auxr[rw + acA]) + prm.dt_f * da.a();
                     auxr[rw + acA] = rr;
-                    auxo[rw + acA] = av.a() + float(prm.b) * rr;
+                    auxo[rw + acA] = av.a() + prm.b_f * rr;
                 }
                 if (piB >= 0) {
-                    const float rr = (ca == 0.f ? 0.f : ca * auxr[rw + acB]) + float(prm.dt) * da.b();
+                    const float rr = (ca == 0.f ? 0.f : ca * auxr[rw + acB]) + prm.dt_f * da.b();
                     auxr[rw + acB] = rr;
-                    auxo[rw + acB] = av.b() + float(prm.b) * rr;
+                    auxo[rw + acB] = av.b() + prm.b_f * rr;
                 }
             }
             PR rold = PR(0.0);
