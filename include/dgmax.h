@@ -184,11 +184,12 @@ int dgm_set_materials(dgm_plan* plan, const double* eps, const double* mu);
  *
  * dgm_forward_record advances the bound state n_steps from time t0 (like
  * dgm_advance), writes the receiver records after every step to
- * records_device [n_steps][S][R][3] (doubles, R = receivers set) and keeps
- * ceil(sqrt(n_steps)) checkpoints in `workspace`.  dgm_adjoint then runs the
- * adjoint backwards in time from dL/drecords (device, same layout as the
- * records): each checkpoint segment is recomputed forward, each step's five
- * stage inputs are recomputed from its start, and the transposed stage
+ * records_device [n_steps][S][R][3] (doubles, R = receivers set) and keeps a
+ * checkpoint every seg = ceil(sqrt(n_steps / 5)) steps in `workspace`.
+ * dgm_adjoint then runs the adjoint backwards in time from dL/drecords
+ * (device, same layout as the records): each checkpoint segment is
+ * recomputed forward once, keeping the five stage inputs of each of its
+ * steps (n_steps / seg + 5 seg states in all), and the transposed stage
  * kernels accumulate the gradient per column in FP64; deps_device and
  * dmu_device (doubles [K]) receive dL/d eps_T and dL/d mu_T summed over
  * columns.  workspace: device memory of dgm_adjoint_workspace bytes,

@@ -924,18 +924,19 @@ __global__ void axpby_kernel(R* y, const R* x, double a, double b, int64_t n) {
 template <typename R>
 __global__ void inject_receivers(R* lu, const double* rec, int nrec, int64_t K, int S, int N,
                                  const double* g) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+    // one thread per (column, component-mode row); receivers in a fixed order,
+    // so that receivers sharing an element accumulate without a race
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(S) * 3 * N) return;
+    const int s = int(i % S);
+    const int jl = int(i / S);
     const int64_t C = K * S;
     for (int r = 0; r < nrec; ++r) {
         const double* w = rec + int64_t(r) * (REC_HDR + 9 * N);
         const int64_t col = int64_t(w[0]) * S + s;
-        const double g0 = g[(int64_t(s) * nrec + r) * 3 + 0];
-        const double g1 = g[(int64_t(s) * nrec + r) * 3 + 1];
-        const double g2 = g[(int64_t(s) * nrec + r) * 3 + 2];
-        for (int jl = 0; jl < 3 * N; ++jl)
-            lu[int64_t(jl) * C + col] += R(w[REC_HDR + jl] * g0 + w[REC_HDR + 3 * N + jl] * g1 +
-                                           w[REC_HDR + 6 * N + jl] * g2);
+        const double* gr = g + (int64_t(s) * nrec + r) * 3;
+        lu[int64_t(jl) * C + col] +=
+            R(w[REC_HDR + jl] * gr[0] + w[REC_HDR + 3 * N + jl] * gr[1] + w[REC_HDR + 6 * N + jl] * gr[2]);
     }
 }
 
@@ -956,7 +957,7 @@ namespace {
 struct AdjLayout {
     size_t fb = 0, ab = 0, sb = 0;   // field, aux, state bytes
     int64_t seg = 0, nseg = 0;
-    size_t ck = 0, sg = 0, st = 0, tmp = 0, res = 0, lu = 0, lr = 0, raw = 0, jmp = 0, grad = 0, total = 0;
+    size_t ck = 0, sg = 0, tmp = 0, res = 0, lu = 0, lr = 0, raw = 0, jmp = 0, grad = 0, total = 0;
 };
 
 AdjLayout adj_layout(const dgm_plan* P, int64_t n) {
@@ -966,12 +967,14 @@ AdjLayout adj_layout(const dgm_plan* P, int64_t n) {
     L.fb = align256(size_t(6) * P->N * C * rs);
     L.ab = align256(size_t(6) * P->N * P->mesh.npml * P->opt.n_columns * rs);
     L.sb = L.fb + L.ab;
-    L.seg = std::max<int64_t>(1, int64_t(std::ceil(std::sqrt(double(std::max<int64_t>(n, 1))))));
+    // checkpoints every seg steps; the reverse sweep recomputes one segment at
+    // a time and keeps the five stage inputs of each of its steps, so states
+    // held = nseg + 5 seg, minimal at seg = sqrt(n / 5)
+    L.seg = std::max<int64_t>(1, int64_t(std::ceil(std::sqrt(double(std::max<int64_t>(n, 1)) / 5.0))));
     L.nseg = (n + L.seg - 1) / L.seg;
     size_t off = 0;
     L.ck = off; off += L.sb * size_t(std::max<int64_t>(L.nseg, 1));
-    L.sg = off; off += L.sb * size_t(L.seg + 1);
-    L.st = off; off += L.sb * 5;
+    L.sg = off; off += L.sb * size_t(5 * L.seg);
     L.tmp = off; off += L.sb * 2;
     L.res = off; off += L.sb;
     L.lu = off; off += L.sb;
@@ -1049,8 +1052,9 @@ extern "C" int dgm_forward_record(dgm_plan* P, int64_t n_steps, double t0, doubl
     return DGM_OK;
 }
 
-// LSRK4 stages of one step from `in`; stage inputs to st[1..nst-1] (st[0] = in),
-// the step's result to `out` when nst == 5 and out.f != nullptr.
+// LSRK4 stages of one step from `in` (= st[0]): the inputs of stages 1..4 go to
+// st[1..4] (to scratch buffers when st is null), the step's result to `out`;
+// with out.f == nullptr the sweep stops after the first nst stages.
 static int lsrk_stages(dgm_plan* P, StateRef in, StateRef* st, int nst, StateRef tmp0, StateRef tmp1,
                        StateRef res, StateRef out, double t) {
     StageParams prm;
@@ -1116,25 +1120,27 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
         int rc = copy_state(P, slot(ws, L.sg, 0, L), slot(ws, L.ck, size_t(sgi), L).f,
                             slot(ws, L.ck, size_t(sgi), L).a, L);
         if (rc) return rc;
-        for (int64_t i = start; i < end - 1; ++i) {   // states x_start .. x_{end-1}
-            rc = lsrk_stages(P, slot(ws, L.sg, size_t(i - start), L), nullptr, 5, tmp0, tmp1, res,
-                             slot(ws, L.sg, size_t(i - start + 1), L), t0 + double(i) * dt);
+        // recompute the segment once, keeping the five stage inputs of each step
+        for (int64_t i = start; i < end; ++i) {
+            StateRef sti[5];
+            for (int k = 0; k < 5; ++k) sti[k] = slot(ws, L.sg, size_t(5 * (i - start) + k), L);
+            const StateRef nxt = (i + 1 < end) ? slot(ws, L.sg, size_t(5 * (i + 1 - start)), L)
+                                               : StateRef{nullptr, nullptr};
+            rc = lsrk_stages(P, sti[0], sti, 4, tmp0, tmp1, res, nxt, t0 + double(i) * dt);
             if (rc) return rc;
         }
         for (int64_t n = end - 1; n >= start; --n) {
             if (P->n_rec > 0) {
+                const unsigned nb = unsigned((int64_t(Sc) * 3 * P->N + 127) / 128);
                 if (f64)
-                    inject_receivers<double><<<(Sc + 63) / 64, 64, 0, P->stream>>>(
+                    inject_receivers<double><<<nb, 128, 0, P->stream>>>(
                         static_cast<double*>(lu.f), recw, P->n_rec, K, Sc, P->N, drec + n * per);
                 else
-                    inject_receivers<float><<<(Sc + 63) / 64, 64, 0, P->stream>>>(
+                    inject_receivers<float><<<nb, 128, 0, P->stream>>>(
                         static_cast<float*>(lu.f), recw, P->n_rec, K, Sc, P->N, drec + n * per);
             }
             const double tn = t0 + double(n) * dt;
-            st[0] = slot(ws, L.sg, size_t(n - start), L);
-            for (int k = 1; k < 5; ++k) st[k] = slot(ws, L.st, size_t(k), L);
-            rc = lsrk_stages(P, st[0], st, 4, tmp0, tmp1, res, StateRef{nullptr, nullptr}, tn);
-            if (rc) return rc;
+            for (int k = 0; k < 5; ++k) st[k] = slot(ws, L.sg, size_t(5 * (n - start) + k), L);
             for (int k = 4; k >= 0; --k) {
                 // lr = a_{k+1} lr + b_k lu  (a_5 := 0 starts each step)
                 const double a = (k == 4) ? 0.0 : LSRK_A[k + 1];
