@@ -142,6 +142,20 @@ def stage_bytes(K, N, S, real_size):
     return (3 * field + geo) + 4 * (4 * field + geo)
 
 
+def world_rate(units, seconds, world, device=None):
+    """Whole-job rate over `world` ranks: the units all ranks processed divided
+    by the slowest rank's time (all ranks must call it; world 1: plain ratio)."""
+    if world <= 1:
+        return units / seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item())
+
+
 def run_gpu(args, precision, steps, warmup, world, rank):
     import torch
     from paper_2002_08733_gb300 import dgmax as D
@@ -185,14 +199,12 @@ def run_gpu(args, precision, steps, warmup, world, rank):
             ev1.synchronize()
         torch.cuda.synchronize(dev)
         ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            tt = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        value = world_rate(dofs * steps, ms * 1e-3, world, dev)
+        ms = dofs * steps * world / value * 1e3       # the slowest rank's time
         g.status()
         energy = float(g.energy()[0])
     out = dict(precision=precision, ms=ms, steps=steps, dofs=dofs, K=K, N=N, S=S, tuned=tuned,
-               value=dofs * steps * world / (ms * 1e-3), clocks=sampler.summary(),
+               value=value, clocks=sampler.summary(),
                energy=energy, launches=5 * steps, real_size=g.info.real_size,
                bytes_fields=g.info.bytes_fields, solver=g, t=t)
     return out
@@ -366,8 +378,9 @@ def run_adjoint(steps):
                 grad_eps_norm=float(eps.grad.norm()), grad_mu_norm=float(mu_p.grad.norm()))
 
 
-def run_e2e(g, steps, t0):
-    """End-to-end: per step, pinned host state -> device, one step, device -> host."""
+def run_e2e(g, steps, t0, world=1):
+    """End-to-end: per step, pinned host state -> device, one step, device -> host,
+    through the C-ABI call with host buffers; whole-job rate over the ranks."""
     import torch
     nbytes = g.info.bytes_fields
     hin = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
@@ -375,6 +388,8 @@ def run_e2e(g, steps, t0):
     hin.copy_(g.fields[g.current()].view(torch.uint8).reshape(-1).cpu())
     g.advance_host(hin, hout, 1, t0)     # warm
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t = t0
     start = time.perf_counter()
     for _ in range(steps):
@@ -382,8 +397,8 @@ def run_e2e(g, steps, t0):
         t += g.dt
     el = time.perf_counter() - start
     dofs = 6 * g.N * g.K * g.S
-    return dict(value=dofs * steps / el, unit=UNIT, h2d_bytes_per_step=int(nbytes),
-                d2h_bytes_per_step=int(nbytes))
+    return dict(value=world_rate(dofs * steps, el, world, g.device), unit=UNIT,
+                h2d_bytes_per_step=int(nbytes), d2h_bytes_per_step=int(nbytes))
 
 
 def cpu_reference(seconds_budget=20.0, n=4):
@@ -492,7 +507,7 @@ def main():
         return
     r64 = run_gpu(args, "fp64", min(args.fp64_steps, args.steps), min(args.warmup, 3), world, rank)
     e2e = None if args.no_e2e else run_e2e(r32["solver"], max(3, min(20, args.steps // 5)),
-                                           r32["t"])
+                                           r32["t"], world)
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
