@@ -372,7 +372,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     {
         constexpr int ROUNDS = (NNBR + NG - 1) / NG;
         constexpr int OWN_ROUNDS = (NOWN + NG - 1) / NG;
-#pragma unroll 1
+        // unrolled (two rounds at 12 groups) so that handing the prefetched
+        // coefficients to the next round is register renaming, not copies
+#pragma unroll
         for (int rr = 0; rr < ROUNDS; ++rr) {
             const int ni = grp + rr * NG;
             R vnx[N];
@@ -506,21 +508,29 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
 
     // ---- phase 4: volume curl + lift per (component, row part) -----------------
     R* rh = trN;   // [6][N][TE], the neighbour traces are dead now
-    // The LSRK residual rows this thread updates in phase 5 (same item) are
-    // requested now so that their latency overlaps the phase-4 arithmetic.
-    constexpr int RPF = (N + NPART - 1) / NPART;
-    constexpr bool PREFETCH_RES = (MODE == MODE_LSRK) && (6 * NPART <= NG);
-    R resv[PREFETCH_RES ? RPF : 1];
+    // Phase 5 works per (field, row part): one item updates the three
+    // components of a field on its rows, so that the 3x3 mass block is applied
+    // once per row and each right-hand-side value is read once.  The LSRK
+    // residual rows of that item are requested now, so that their latency
+    // overlaps the phase-4 arithmetic.
+    constexpr int NP5 = (NG / 2 < N ? NG / 2 : N) > 0 ? (NG / 2 < N ? NG / 2 : N) : 1;   // row parts per field
+    constexpr int RP5 = (N + NP5 - 1) / NP5;          // rows per part (at most)
+    constexpr bool P5_EVEN = (N % NP5) == 0;          // every part has exactly RP5 rows
+    constexpr bool PREFETCH_RES = (MODE == MODE_LSRK);
+    R resv[PREFETCH_RES ? 3 : 1][PREFETCH_RES ? RP5 : 1];
     // stage coefficients in the kernel's precision: FP32 kernels read the FP32
     // copies, so that no conversion runs on the FP64 pipe
     auto coef = [&](double d, float f) { return sizeof(R) == 4 ? R(f) : R(d); };
-    if (PREFETCH_RES && grp < 6 * NPART && active && coef(prm.a, prm.a_f) != R(0)) {
-        const int comp = grp / NPART, part = grp % NPART;
-        const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
+    if (PREFETCH_RES && grp < 2 * NP5) {
+        const int fb = (grp / NP5) * 3, part = grp % NP5;
+        const int lo = part * N / NP5, hi = (part + 1) * N / NP5;
+        const bool load = active && coef(prm.a, prm.a_f) != R(0);
         const R* __restrict__ res = static_cast<const R*>(prm.res);
 #pragma unroll
-        for (int i = 0; i < RPF; ++i)
-            if (lo + i < hi) resv[i] = res[int64_t(comp * N + lo + i) * C + col];
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < RP5; ++i)
+                resv[k][i] = (load && (P5_EVEN || lo + i < hi)) ? res[int64_t((fb + k) * N + lo + i) * C + col] : R(0);
     }
     for (int it = grp; it < 6 * NPART; it += NG) {
         const int comp = it / NPART;
@@ -554,20 +564,19 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     if (MODE == MODE_RAW) return;   // forward quantities for the adjoint only
     __syncthreads();
 
-    // ---- phase 5: mass-block inverse, PML, update ------------------------------
-    for (int it = grp; it < 6 * NPART; it += NG) {
-        const int comp = it / NPART;
-        const int part = it % NPART;
-        if (!DO_E && comp < 3) continue;
-        if (!DO_H && comp >= 3) continue;
+    // ---- phase 5: mass-block inverse, PML, update per (field, row part) --------
+    for (int it = grp; it < 2 * NP5; it += NG) {
+        const int field = it / NP5;
+        const int part = it % NP5;
+        if (!DO_E && field == 0) continue;
+        if (!DO_H && field == 1) continue;
         if (!active) continue;
-        const int j = comp % 3;
-        const int fb = comp < 3 ? 0 : 3;   // first component of this field
+        const int fb = 3 * field;   // first component of this field
         R ait[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
         const R det = eg[G_DET * TE + c];
-        const R mat = comp < 3 ? eg[G_EPS * TE + c] : eg[G_MU * TE + c];
+        const R mat = field == 0 ? eg[G_EPS * TE + c] : eg[G_MU * TE + c];
         // A^T = adj(A^-T) det A
         R AT[3][3];
         AT[0][0] = ait[4] * ait[8] - ait[5] * ait[7];
@@ -583,20 +592,20 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b) AT[a][b] *= det;
-        // row j of A^T, selected without dynamic indexing (keeps AT in registers)
-        R atj[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) atj[b] = j == 0 ? AT[0][b] : (j == 1 ? AT[1][b] : AT[2][b]);
-        // row j of the 3x3 mass-block inverse A^T A / (mat |det|)
-        R brow[3];
+        // the 3x3 mass-block inverse A^T A / (mat |det|), symmetric
+        R B[3][3];
         const R inv = R(1) / (mat * fabs(det));
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            brow[k] = inv * (atj[0] * AT[k][0] + atj[1] * AT[k][1] + atj[2] * AT[k][2]);
-        // PML rows: (A^T D A^-T)[j][k] = sum_a A^T[j][a] D_a A^-T[a][k]
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = j; k < 3; ++k) {
+                B[j][k] = inv * (AT[j][0] * AT[k][0] + AT[j][1] * AT[k][1] + AT[j][2] * AT[k][2]);
+                B[k][j] = B[j][k];
+            }
+        // PML: (A^T D A^-T)[j][k] = sum_a A^T[j][a] D_a A^-T[a][k] for D = eta, Sigma, xi
         int32_t pi = -1;
         if (prm.pml != nullptr) pi = prm.pml[e];
-        R eta_row[3] = {0, 0, 0}, sig_row[3] = {0, 0, 0}, xi_row[3] = {0, 0, 0};
+        R ETA[3][3], SIG[3][3], XI[3][3];
         if (pi >= 0) {
             const R sx = eg[(G_SIG + 0) * TE + c], sy = eg[(G_SIG + 1) * TE + c],
                     sz = eg[(G_SIG + 2) * TE + c];
@@ -604,15 +613,22 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             const R et3[3] = {sy + sz - sx, sz + sx - sy, sx + sy - sz};
             const R xi3[3] = {(sx - sy) * (sx - sz), (sy - sz) * (sy - sx), (sz - sx) * (sz - sy)};
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const R w = atj[a] * ait[3 * a + k];
-                    eta_row[k] += w * et3[a];
-                    sig_row[k] += w * sg3[a];
-                    xi_row[k] += w * xi3[a];
+                for (int k = 0; k < 3; ++k) {
+                    ETA[j][k] = R(0);
+                    SIG[j][k] = R(0);
+                    XI[j][k] = R(0);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const R w = AT[j][a] * ait[3 * a + k];
+                        ETA[j][k] += w * et3[a];
+                        SIG[j][k] += w * sg3[a];
+                        XI[j][k] += w * xi3[a];
+                    }
                 }
         }
+        const R imat = R(1) / mat;
         const int64_t C2 = int64_t(prm.npml) * S;
         const int64_t acol = int64_t(pi) * S + s;
         R* uo = static_cast<R*>(prm.u_out);
@@ -621,48 +637,55 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         R* __restrict__ auxo = static_cast<R*>(prm.aux_out);
         R* __restrict__ auxr = static_cast<R*>(prm.aux_res);
         const R dt = coef(prm.dt, prm.dt_f), ca = coef(prm.a, prm.a_f), cb = coef(prm.b, prm.b_f);
-        const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
+        const int lo = part * N / NP5, hi = (part + 1) * N / NP5;
+        const int64_t gb = int64_t(fb * N + lo) * C + col;          // (fb, lo) in the fields
+        const int64_t ab = int64_t(fb * N + lo) * C2 + acol;        // (fb, lo) in the auxiliaries
         // rows l = lo + i with a compile-time i, so that the prefetched
         // residuals stay in registers
 #pragma unroll
-        for (int i = 0; i < RPF; ++i) {
+        for (int i = 0; i < RP5; ++i) {
             const int l = lo + i;
-            if (l >= hi) break;
-            const R r0 = rh[((fb + 0) * N + l) * TE + c];
-            const R r1 = rh[((fb + 1) * N + l) * TE + c];
-            const R r2 = rh[((fb + 2) * N + l) * TE + c];
-            R du = brow[0] * r0 + brow[1] * r1 + brow[2] * r2;
-            const R uv = us[(comp * N + l) * TE + c];
-            const int64_t gi = int64_t(comp * N + l) * C + col;
+            if (!P5_EVEN && l >= hi) break;
+            R r[3], uv[3], du[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                r[k] = rh[((fb + k) * N + l) * TE + c];
+                uv[k] = us[((fb + k) * N + l) * TE + c];
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) du[k] = B[k][0] * r[0] + B[k][1] * r[1] + B[k][2] * r[2];
             if (pi >= 0) {
-                const R u0 = us[((fb + 0) * N + l) * TE + c];
-                const R u1 = us[((fb + 1) * N + l) * TE + c];
-                const R u2 = us[((fb + 2) * N + l) * TE + c];
-                const int64_t ai = int64_t(fb * N + l) * C2 + acol;
-                const R a0 = aux[ai], a1 = aux[ai + int64_t(N) * C2], a2 = aux[ai + 2 * int64_t(N) * C2];
-                const R av = j == 0 ? a0 : (j == 1 ? a1 : a2);
-                du -= eta_row[0] * u0 + eta_row[1] * u1 + eta_row[2] * u2 + av / mat;
-                const R da = -(sig_row[0] * a0 + sig_row[1] * a1 + sig_row[2] * a2) +
-                             mat * (xi_row[0] * u0 + xi_row[1] * u1 + xi_row[2] * u2);
-                const int64_t aj = int64_t(comp * N + l) * C2 + acol;
-                if (MODE == MODE_RHS) {
-                    auxo[aj] = da;
-                } else if (MODE == MODE_LSRK) {
-                    const R rr = (ca == R(0) ? R(0) : ca * auxr[aj]) + dt * da;
-                    auxr[aj] = rr;
-                    auxo[aj] = av + cb * rr;
+                R av[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) av[k] = aux[ab + int64_t(k * N + i) * C2];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    du[k] -= ETA[k][0] * uv[0] + ETA[k][1] * uv[1] + ETA[k][2] * uv[2] + av[k] * imat;
+                    const R da = -(SIG[k][0] * av[0] + SIG[k][1] * av[1] + SIG[k][2] * av[2]) +
+                                 mat * (XI[k][0] * uv[0] + XI[k][1] * uv[1] + XI[k][2] * uv[2]);
+                    const int64_t aj = ab + int64_t(k * N + i) * C2;
+                    if (MODE == MODE_RHS) {
+                        auxo[aj] = da;
+                    } else if (MODE == MODE_LSRK) {
+                        const R rr = (ca == R(0) ? R(0) : ca * auxr[aj]) + dt * da;
+                        auxr[aj] = rr;
+                        auxo[aj] = av[k] + cb * rr;
+                    }
                 }
             }
-            if (MODE == MODE_RHS) {
-                uo[gi] = du;
-            } else if (MODE == MODE_LSRK) {
-                R rold = R(0);
-                if (ca != R(0)) rold = PREFETCH_RES ? resv[PREFETCH_RES ? i : 0] : res[gi];
-                const R rr = ca * rold + dt * du;
-                res[gi] = rr;
-                uo[gi] = uv + cb * rr;
-            } else {
-                uo[gi] = uv + dt * du;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int64_t gi = gb + int64_t(k * N + i) * C;
+                if (MODE == MODE_RHS) {
+                    uo[gi] = du[k];
+                } else if (MODE == MODE_LSRK) {
+                    // resv is 0 when a = 0 (first stage), so no branch on a here
+                    const R rr = ca * resv[PREFETCH_RES ? k : 0][PREFETCH_RES ? i : 0] + dt * du[k];
+                    res[gi] = rr;
+                    uo[gi] = uv[k] + cb * rr;
+                } else {
+                    uo[gi] = uv[k] + dt * du[k];
+                }
             }
         }
     }
