@@ -318,9 +318,21 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
         const bool bnd = d[FC_BND * TE] != R(0);
         const R twoF = d[FC_TWOF * TE];
         const R ce = d[FC_CE * TE], be = d[FC_BE * TE], chh = d[FC_CH * TE], bh = d[FC_BH * TE];
-        R bNe[3][3], bNh[3][3], ATn[3][3];
-        mass_block(aitn, d[FA_DETN * TE], d[FA_EPSN * TE], bNe, ATn);
-        mass_block(aitn, d[FA_DETN * TE], d[FA_MUN * TE], bNh, ATn);
+        // phi of the neighbour's side = +-2|F| A_n^-T B_n t: the two 3x3 products
+        // formed once per item (fewer live values across the mode loop)
+        R ME[3][3], MH[3][3];
+        {
+            R bNe[3][3], bNh[3][3], ATn[3][3];
+            mass_block(aitn, d[FA_DETN * TE], d[FA_EPSN * TE], bNe, ATn);
+            mass_block(aitn, d[FA_DETN * TE], d[FA_MUN * TE], bNh, ATn);
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    ME[r][k] = twoF * (aitn[3 * r] * bNe[0][k] + aitn[3 * r + 1] * bNe[1][k] + aitn[3 * r + 2] * bNe[2][k]);
+                    MH[r][k] = -twoF * (aitn[3 * r] * bNh[0][k] + aitn[3 * r + 1] * bNh[1][k] + aitn[3 * r + 2] * bNh[2][k]);
+                }
+        }
         // impedances for dJ/dZ (upwind only)
         const R zm = sqrt(eg[G_MU * TE + c] / eg[G_EPS * TE + c]);
         const R zp = bnd ? zm : sqrt(d[FA_MUN * TE] / d[FA_EPSN * TE]);
@@ -364,21 +376,14 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
                     vH[r] = R(0);
                 }
             } else {
-                R tn[3], tnh[3], gEn[3], gHn[3];
+                R tn[3], tnh[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     tn[k] = nbt[k * NF * TE];
                     tnh[k] = nbt[(3 + k) * NF * TE];
                 }
-                matvec3(bNe, tn, gEn);
-                matvec3(bNh, tnh, gHn);
-                ait_mul(aitn, gEn, phiEn);
-                ait_mul(aitn, gHn, phiHn);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    phiEn[k] *= twoF;
-                    phiHn[k] *= -twoF;
-                }
+                matvec3(ME, tn, phiEn);
+                matvec3(MH, tnh, phiHn);
                 // neighbour's face (normal -n, c_E <-> c_H):
                 // adj(dH)_N = cH n x phiE_N + bH n x (n x phiH_N); adj(dE)_N = -bE n x (n x phiE_N) + cE n x phiH_N
                 R a1[3], a2[3], b1[3], b2[3];
