@@ -100,6 +100,45 @@ def test_autotuned_variants_match_oracle(D):
         assert rel_l2(g2.state(), ref) < 1e-5, v
 
 
+_HIGH_P_REF = {}
+
+
+def _high_p_case(p):
+    """48-element PML mesh with a source (one partial tile) and the oracle's two
+    LSRK4 steps from a seeded state, computed once per degree."""
+    if p not in _HIGH_P_REF:
+        xyz, tets = W.kuhn_mesh(2, (-1, -1, -1), (1, 1, 1), jitter=0.1, seed=73)
+        pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+        srcs = [W.dipole((0.1, 0.05, -0.02), 2.0, 1.0)]
+        dt = W.stable_dt(1.0, p)
+        u = W.random_state(len(tets), 1, p, seed=74) * 1e-2
+        o = build(xyz, tets, p, 1.0, 1.0, "upwind", pml=pml, S=1, sources=srcs)
+        ref, ref_aux = o.unpack(o.lsrk4(o.pack(u, np.zeros_like(u)), 0.0, dt, 2))
+        _HIGH_P_REF[p] = (xyz, tets, pml, srcs, dt, u, ref, ref_aux)
+    return _HIGH_P_REF[p]
+
+
+@pytest.mark.parametrize("p,prec,nv", [(4, "fp32", 3), (4, "fp64", 1), (5, "fp32", 3)])
+def test_autotuner_variants_high_degree(D, p, prec, nv):
+    """Above p = 3 the FP32 autotuner has the three single-column shapes (the
+    paired tile does not fit in shared memory) and FP64 has one; each gives the
+    oracle's stage on a PML problem with a source."""
+    import torch
+    xyz, tets, pml, srcs, dt, u, ref, ref_aux = _high_p_case(p)
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", dt, S=1, pml=pml)
+    chosen, ms = g.autotune()
+    assert len(ms) == nv and 0 <= chosen < nv and np.all(ms > 0)
+    tol = 1e-5 if prec == "fp32" else 1e-12
+    for v in range(nv):
+        g2 = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", dt, S=1, pml=pml)
+        g2.set_sources(srcs)
+        g2.set_state(u)
+        g2.set_variant(v)
+        g2.advance(2)
+        assert rel_l2(g2.state(), ref) < tol, v
+        assert rel_l2(g2.from_device(g2.aux[g2.current()]), ref_aux[g2.pml_elements()]) < tol, v
+
+
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("v", [3, 4])
 def test_paired_variants_pml_sources_match_oracle(D, p, v):
