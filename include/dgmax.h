@@ -213,6 +213,13 @@ int dgm_autotune(dgm_plan* plan, void* workspace, int32_t reps, float* ms_out);
 int dgm_autotune_info(const dgm_plan* plan, int32_t* n_variants, int32_t* chosen);
 /* Select a tile-shape variant explicitly (0 .. n_variants-1). */
 int dgm_set_variant(dgm_plan* plan, int32_t variant);
+/* Index arithmetic of the stage kernels.  By default (force = 0) a launch
+ * uses 32-bit indices when every index it forms fits (field and face-jump
+ * rows times columns, auxiliaries, geometry, the per-face table are all below
+ * 2^32) and 64-bit indices otherwise; force = 1 selects the 64-bit kernels
+ * always, to check that path on problems of any size.  Results are the same
+ * either way.  DGM_EINVAL for other values. */
+int dgm_set_index64(dgm_plan* plan, int32_t force);
 
 /* Index (0 or 1) of the bound field/aux buffer that holds the current state. */
 int dgm_current(const dgm_plan* plan);

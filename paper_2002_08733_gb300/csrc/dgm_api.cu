@@ -80,6 +80,7 @@ struct dgm_plan {
     int cur = 0;
     int device = -1;
     int variant = 0;          // LSRK stage tile shape chosen by dgm_autotune
+    int force_index64 = 0;    // dgm_set_index64
     float variant_ms[8] = {0};
 };
 
@@ -382,6 +383,7 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.upwind = P->opt.flux == DGM_UPWIND;
     prm.dt = P->opt.dt;
     prm.variant = P->variant;
+    prm.force_index64 = P->force_index64;
 }
 
 int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double* pos,
@@ -1259,6 +1261,13 @@ extern "C" int dgm_set_variant(dgm_plan* P, int32_t v) {
     if (!P) return fail(DGM_EINVAL, "null plan");
     if (v < 0 || v >= P->kt->n_variants) return fail(DGM_EINVAL, "variant out of range");
     P->variant = v;
+    return DGM_OK;
+}
+
+extern "C" int dgm_set_index64(dgm_plan* P, int32_t force) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (force != 0 && force != 1) return fail(DGM_EINVAL, "force must be 0 or 1");
+    P->force_index64 = force;
     return DGM_OK;
 }
 

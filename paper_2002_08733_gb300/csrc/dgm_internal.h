@@ -66,6 +66,7 @@ struct StageParams {
     void* raw;            // MODE_RAW: right-hand side before the mass inverse [6][N][K][S]
     void* jumps;          // MODE_RAW: physical face jumps dE, dH [4][6][NF][K][S]
     int32_t variant;      // tile-shape variant of the LSRK stage kernel (autotuner)
+    int32_t force_index64;// 1: 64-bit index arithmetic even where 32 bits suffice
 };
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms

@@ -76,16 +76,33 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
 }
 #else
-int launch_mode(const StageParams& prm, cudaStream_t st) {
+template <typename IX>
+int launch_ix(const StageParams& q, unsigned grid, cudaStream_t st) {
     constexpr size_t smem = stage_smem_bytes<kP, Real, kTE>();
     static bool configured = false;
-    auto k = stage_kernel<kP, Real, kTE, kNT, DGM_MODE>;
+    auto k = stage_kernel<kP, Real, kTE, kNT, DGM_MODE, IX>;
     if (!configured) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
             cudaSuccess)
             return DGM_ECUDA;
         configured = true;
     }
+    k<<<grid, kNT, smem, st>>>(q);
+    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+}
+
+// true when every index the stage kernel forms for this plan is below 2^32:
+// field rows (6N x C), face jumps (24 NF x C), auxiliaries (6N x npml S),
+// geometry (G_COUNT x K), the per-face table (4 FNB_COUNT x K), neighbours (4K)
+bool fits_32bit(const StageParams& p) {
+    const uint64_t lim = uint64_t(1) << 32;
+    const uint64_t K = uint64_t(p.K), C = K * uint64_t(p.S);
+    const uint64_t N = uint64_t(nmodes(kP)), NF = uint64_t(nfmodes(kP));
+    return 6 * N * C < lim && 24 * NF * C < lim && 6 * N * uint64_t(p.npml) * uint64_t(p.S) < lim &&
+           uint64_t(G_COUNT) * K < lim && 4 * uint64_t(FNB_COUNT) * K < lim && 4 * K < lim;
+}
+
+int launch_mode(const StageParams& prm, cudaStream_t st) {
     const int64_t C = prm.K * prm.S;
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + kTE - 1) / kTE);
@@ -93,8 +110,8 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     q.dt_f = float(prm.dt);
     q.a_f = float(prm.a);
     q.b_f = float(prm.b);
-    k<<<grid, kNT, smem, st>>>(q);
-    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+    return (!q.force_index64 && fits_32bit(q)) ? launch_ix<uint32_t>(q, grid, st)
+                                               : launch_ix<int64_t>(q, grid, st);
 }
 #endif
 

@@ -244,7 +244,11 @@ __device__ __forceinline__ void rhs_part(int part, int comp, int c, const R* us,
 
 // Two resident CTAs per SM where the registers allow it: FP32 up to p = 3
 // (<= 85 registers at 384 threads), FP64 at 192 threads (<= 170 registers).
-template <int P, typename R, int TE, int NT, int MODE>
+// IX: type of the element/column/row index arithmetic.  uint32_t when every
+// index of the plan fits (the launcher checks), which saves the 64-bit
+// address arithmetic that is a large part of this kernel's integer work;
+// int64_t otherwise.
+template <int P, typename R, int TE, int NT, int MODE, typename IX = int64_t>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_kernel(const StageParams prm) {
     constexpr int N = nmodes(P);
     constexpr int NF = nfmodes(P);
@@ -262,16 +266,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
 
     const int c = threadIdx.x % TE;
     const int grp = threadIdx.x / TE;
-    const int64_t K = prm.K;
+    const IX K = prm.K;
     const int S = prm.S;
-    const int64_t C = K * S;
-    const int64_t col = int64_t(blockIdx.x) * TE + c;
+    const IX C = K * S;
+    const IX col = IX(blockIdx.x) * TE + c;
     const bool active = col < C;
-    const int64_t e = active ? col / S : 0;
+    const IX e = active ? col / S : 0;
     const int s = active ? int(col - e * S) : 0;
     const R* u = static_cast<const R*>(prm.u);   // may alias u_out (leapfrog)
     const R* gr = static_cast<const R*>(prm.geo_r);
-    if (grp < 4) nbs[grp * TE + c] = active ? prm.nbr[int64_t(grp) * K + e] : -1;
+    if (grp < 4) nbs[grp * TE + c] = active ? prm.nbr[IX(grp) * K + e] : -1;
 
     // ---- phase 1: tile coefficients, element and face constants --------------
     // Groups 0..3 compute the face constants of face f = group from the
@@ -291,29 +295,29 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     // neighbour's coefficients of that component given the face's code
     auto request_nbr = [&](int ni, int32_t code, R (&dst)[N]) {
         if (ni < NNBR && nbr_item_active(ni % 6) && active && code >= 0 && (code >> 2) < K) {
-            const int64_t ncol = int64_t(code >> 2) * S + s;
+            const IX ncol = IX(code >> 2) * S + s;
 #pragma unroll
-            for (int l = 0; l < N; ++l) dst[l] = u[int64_t((ni % 6) * N + l) * C + ncol];
+            for (int l = 0; l < N; ++l) dst[l] = u[IX((ni % 6) * N + l) * C + ncol];
         }
     };
     auto face_consts = [&](int f) {
         R ait[9], aitn[9];
-        const R* fn = static_cast<const R*>(prm.fnb_r) + int64_t(f * FNB_COUNT) * K + e;
-        const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
+        const R* fn = static_cast<const R*>(prm.fnb_r) + IX(f * FNB_COUNT) * K + e;
+        const int32_t code = active ? prm.nbr[IX(f) * K + e] : -1;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) ait[k] = active ? gr[int64_t(G_AIT + k) * K + e] : R(k % 4 == 0);
+        for (int k = 0; k < 9; ++k) ait[k] = active ? gr[IX(G_AIT + k) * K + e] : R(k % 4 == 0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) aitn[k] = active ? fn[int64_t(FNB_AIT + k) * K] : ait[k];
-        const R det = active ? gr[int64_t(G_DET) * K + e] : R(1);
-        const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
-        const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
-        const R zn = active ? fn[int64_t(FNB_Z) * K] : R(1);
+        for (int k = 0; k < 9; ++k) aitn[k] = active ? fn[IX(FNB_AIT + k) * K] : ait[k];
+        const R det = active ? gr[IX(G_DET) * K + e] : R(1);
+        const R epsm = active ? gr[IX(G_EPS) * K + e] : R(1);
+        const R mum = active ? gr[IX(G_MU) * K + e] : R(1);
+        const R zn = active ? fn[IX(FNB_Z) * K] : R(1);
         face_constants_tab<R, TE>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
                                   prm.upwind, fg + f * FG * TE + c);
     };
     // neighbour code of this group's round-0 item, loaded with the other
     // independent loads so that the dependent gather starts one round trip in
-    const int32_t code0 = (grp < NNBR && active) ? prm.nbr[int64_t(grp / 6) * K + e] : -1;
+    const int32_t code0 = (grp < NNBR && active) ? prm.nbr[IX(grp / 6) * K + e] : -1;
     if (grp < FACE_GROUPS) {
         face_consts(grp);
         request_nbr(grp, code0, vn);
@@ -327,13 +331,13 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
 #pragma unroll
         for (int i = 0; i < BATCH; ++i) {
             const int r = lg + i * LG;
-            tmp[i] = (i < UR && r < 6 * N && active) ? u[int64_t(r) * C + col] : R(0);
+            tmp[i] = (i < UR && r < 6 * N && active) ? u[IX(r) * C + col] : R(0);
         }
         R tmpe[ER];
 #pragma unroll
         for (int i = 0; i < ER; ++i) {
             const int k = lg + i * LG;
-            tmpe[i] = (k < EG && active) ? gr[int64_t(k) * K + e]
+            tmpe[i] = (k < EG && active) ? gr[IX(k) * K + e]
                                          : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
         }
         request_nbr(grp, code0, vn);
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
 #pragma unroll
                 for (int i = 0; i < BATCH; ++i) {
                     const int r = lg + (i0 + i) * LG;
-                    tmp[i] = (i0 + i < UR && r < 6 * N && active) ? u[int64_t(r) * C + col] : R(0);
+                    tmp[i] = (i0 + i < UR && r < 6 * N && active) ? u[IX(r) * C + col] : R(0);
                 }
             }
 #pragma unroll
@@ -475,8 +479,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
                     R* jp = static_cast<R*>(prm.jumps);
 #pragma unroll
                     for (int r = 0; r < 3; ++r) {
-                        jp[int64_t((f * 6 + r) * NF + m) * C + col] = dE[r];
-                        jp[int64_t((f * 6 + 3 + r) * NF + m) * C + col] = dH[r];
+                        jp[IX((f * 6 + r) * NF + m) * C + col] = dE[r];
+                        jp[IX((f * 6 + 3 + r) * NF + m) * C + col] = dH[r];
                     }
                 }
                 R nxdE[3], nxdH[3], nnxdE[3], nnxdH[3];
@@ -530,7 +534,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int i = 0; i < RP5; ++i)
-                resv[k][i] = (load && (P5_EVEN || lo + i < hi)) ? res[int64_t((fb + k) * N + lo + i) * C + col] : R(0);
+                resv[k][i] = (load && (P5_EVEN || lo + i < hi)) ? res[IX((fb + k) * N + lo + i) * C + col] : R(0);
     }
     for (int it = grp; it < 6 * NPART; it += NG) {
         const int comp = it / NPART;
@@ -542,8 +546,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         rhs_part<P, R, TE, NPART>(part, comp, c, us, trO, sgn, acc);
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
         if (comp < 3 && prm.src != nullptr && active) {
-            const double* rec = prm.src + int64_t(s) * (SRC_HDR + 3 * N);
-            if (int64_t(rec[0]) == e) {
+            const double* rec = prm.src + IX(s) * (SRC_HDR + 3 * N);
+            if (rec[0] >= 0.0 && IX(rec[0]) == e) {   // -1 marks a column without a source
                 const double tt = prm.tdev ? *prm.tdev + prm.t : prm.t;
                 const R g = R(source_time(tt, rec[1], rec[2], rec[3]));
 #pragma unroll
@@ -558,7 +562,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             R* rw = static_cast<R*>(prm.raw);
 #pragma unroll
             for (int l = 0; l < N; ++l)
-                if (l >= lo && l < hi) rw[int64_t(comp * N + l) * C + col] = acc[l];
+                if (l >= lo && l < hi) rw[IX(comp * N + l) * C + col] = acc[l];
         }
     }
     if (MODE == MODE_RAW) return;   // forward quantities for the adjoint only
@@ -629,8 +633,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
                 }
         }
         const R imat = R(1) / mat;
-        const int64_t C2 = int64_t(prm.npml) * S;
-        const int64_t acol = int64_t(pi) * S + s;
+        const IX C2 = IX(prm.npml) * S;
+        const IX acol = IX(pi) * S + s;
         R* uo = static_cast<R*>(prm.u_out);
         R* __restrict__ res = static_cast<R*>(prm.res);
         const R* __restrict__ aux = static_cast<const R*>(prm.aux);
@@ -638,8 +642,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         R* __restrict__ auxr = static_cast<R*>(prm.aux_res);
         const R dt = coef(prm.dt, prm.dt_f), ca = coef(prm.a, prm.a_f), cb = coef(prm.b, prm.b_f);
         const int lo = part * N / NP5, hi = (part + 1) * N / NP5;
-        const int64_t gb = int64_t(fb * N + lo) * C + col;          // (fb, lo) in the fields
-        const int64_t ab = int64_t(fb * N + lo) * C2 + acol;        // (fb, lo) in the auxiliaries
+        const IX gb = IX(fb * N + lo) * C + col;          // (fb, lo) in the fields
+        const IX ab = IX(fb * N + lo) * C2 + acol;        // (fb, lo) in the auxiliaries
         // rows l = lo + i with a compile-time i, so that the prefetched
         // residuals stay in registers
 #pragma unroll
@@ -657,13 +661,13 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             if (pi >= 0) {
                 R av[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) av[k] = aux[ab + int64_t(k * N + i) * C2];
+                for (int k = 0; k < 3; ++k) av[k] = aux[ab + IX(k * N + i) * C2];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     du[k] -= ETA[k][0] * uv[0] + ETA[k][1] * uv[1] + ETA[k][2] * uv[2] + av[k] * imat;
                     const R da = -(SIG[k][0] * av[0] + SIG[k][1] * av[1] + SIG[k][2] * av[2]) +
                                  mat * (XI[k][0] * uv[0] + XI[k][1] * uv[1] + XI[k][2] * uv[2]);
-                    const int64_t aj = ab + int64_t(k * N + i) * C2;
+                    const IX aj = ab + IX(k * N + i) * C2;
                     if (MODE == MODE_RHS) {
                         auxo[aj] = da;
                     } else if (MODE == MODE_LSRK) {
@@ -675,7 +679,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const int64_t gi = gb + int64_t(k * N + i) * C;
+                const IX gi = gb + IX(k * N + i) * C;
                 if (MODE == MODE_RHS) {
                     uo[gi] = du[k];
                 } else if (MODE == MODE_LSRK) {

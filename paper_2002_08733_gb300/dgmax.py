@@ -75,6 +75,7 @@ _SIGS = {
     "dgm_autotune": [_P, _P, ctypes.c_int32, _P],
     "dgm_autotune_info": [_P, _P, _P],
     "dgm_set_variant": [_P, ctypes.c_int32],
+    "dgm_set_index64": [_P, ctypes.c_int32],
     "dgm_adjoint_workspace": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
     "dgm_forward_record": [_P, ctypes.c_int64, ctypes.c_double, _P, _P],
     "dgm_adjoint": [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
@@ -324,6 +325,10 @@ class Solver(Plan):
 
     def set_variant(self, v):
         _check(_lib.dgm_set_variant(self.handle, int(v)))
+
+    def set_index64(self, force=True):
+        """Force 64-bit index arithmetic in the stage kernels (default: automatic)."""
+        _check(_lib.dgm_set_index64(self.handle, int(bool(force))))
 
     def set_materials(self, eps, mu):
         eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (self.K,)))

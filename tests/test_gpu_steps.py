@@ -68,6 +68,38 @@ def test_lsrk4_tile_load_paths(D, prec, tol, S):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("S", [1, 2])
+def test_index_width_paths(D, prec, tol, S):
+    """The stage kernels use 32-bit index arithmetic when every index fits and
+    64-bit otherwise; forcing the 64-bit kernels on a small problem must give
+    the same results bit for bit (five LSRK4 steps and one right-hand side,
+    with PML, a source and S columns), and both match the oracle."""
+    xyz, tets = W.kuhn_mesh(3, (-1, -1, -1), (1, 1, 1), jitter=0.1, seed=25)
+    K, p = len(tets), 2
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+    srcs = [W.dipole((0.11, -0.07, 0.05), 2.0, 1.0)] + [None] * (S - 1)
+    dt = W.stable_dt(2 / 3, p)
+    u = W.random_state(K, S, p, seed=26) * 1e-2
+    got = []
+    for force in (False, True):
+        g = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", dt, S=S, pml=pml)
+        if force:
+            g.set_index64(True)
+        g.set_sources(srcs)
+        du, dad = g.rhs(u)
+        g.set_state(u)
+        g.advance(5, 0.0)
+        got.append([g.state(), g.from_device(g.aux[g.current()]), g.from_device(du),
+                    g.from_device(dad)])
+    for a, b in zip(got[0], got[1]):
+        assert np.array_equal(a, b)
+    o = build(xyz, tets, p, 1.0, 1.0, "upwind", pml=pml, S=S, sources=srcs)
+    ref, ref_aux = o.unpack(o.lsrk4(o.pack(u, np.zeros_like(u)), 0.0, dt, 5))
+    assert rel_l2(got[0][0], ref) < tol
+    assert rel_l2(got[0][1], ref_aux[g.pml_elements()]) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_lsrk4_pml_dipole_trajectory(D, prec, tol):
     xyz, tets = W.kuhn_mesh(4, (-1, -1, -1), (1, 1, 1))
     K, p, S = len(tets), 2, 1
