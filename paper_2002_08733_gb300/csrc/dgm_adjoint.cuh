@@ -137,7 +137,8 @@ __device__ __host__ constexpr size_t adjoint_smem_bytes() {
            sizeof(double) * size_t(TE) * (4 * CH + 2 * 6 * NPART);
 }
 
-template <int P, typename R, int TE, int NT>
+// IX: index type (uint32_t when every index of the plan fits, else int64_t)
+template <int P, typename R, int TE, int NT, typename IX = int64_t>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_kernel(const AdjParams prm) {
     constexpr int N = nmodes(P);
     constexpr int NF = nfmodes(P);
@@ -156,12 +157,12 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
 
     const int c = threadIdx.x % TE;
     const int grp = threadIdx.x / TE;
-    const int64_t K = prm.K;
+    const IX K = prm.K;
     const int S = prm.S;
-    const int64_t C = K * S;
-    const int64_t col = int64_t(blockIdx.x) * TE + c;
+    const IX C = K * S;
+    const IX col = IX(blockIdx.x) * TE + c;
     const bool active = col < C;
-    const int64_t e = active ? col / S : 0;
+    const IX e = active ? col / S : 0;
     const int s = active ? int(col - e * S) : 0;
     const R* lam = static_cast<const R*>(prm.lr);
 
@@ -177,22 +178,22 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
     bool vn_ready = false;
     auto face_consts = [&](int f) {
         R ait[9], aitn[9];
-        const R* fn = static_cast<const R*>(prm.fnb_r) + int64_t(f * FNB_COUNT) * K + e;
-        const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
+        const R* fn = static_cast<const R*>(prm.fnb_r) + IX(f * FNB_COUNT) * K + e;
+        const int32_t code = active ? prm.nbr[IX(f) * K + e] : -1;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) ait[k] = active ? gr[int64_t(G_AIT + k) * K + e] : R(k % 4 == 0);
+        for (int k = 0; k < 9; ++k) ait[k] = active ? gr[IX(G_AIT + k) * K + e] : R(k % 4 == 0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) aitn[k] = active ? fn[int64_t(FNB_AIT + k) * K] : ait[k];
-        const R det = active ? gr[int64_t(G_DET) * K + e] : R(1);
-        const R epsm = active ? gr[int64_t(G_EPS) * K + e] : R(1);
-        const R mum = active ? gr[int64_t(G_MU) * K + e] : R(1);
-        const R zn = active ? fn[int64_t(FNB_Z) * K] : R(1);
+        for (int k = 0; k < 9; ++k) aitn[k] = active ? fn[IX(FNB_AIT + k) * K] : ait[k];
+        const R det = active ? gr[IX(G_DET) * K + e] : R(1);
+        const R epsm = active ? gr[IX(G_EPS) * K + e] : R(1);
+        const R mum = active ? gr[IX(G_MU) * K + e] : R(1);
+        const R zn = active ? fn[IX(FNB_Z) * K] : R(1);
         const bool has = code >= 0 && (code >> 2) < K;
         R* fc = fg + f * FGA * TE + c;
         face_constants_tab<R, TE>(f, ait, det, epsm, mum, has, aitn, zn, prm.upwind, fc);
-        fc[FA_DETN * TE] = has ? fn[int64_t(FNB_DET) * K] : det;
-        fc[FA_EPSN * TE] = has ? fn[int64_t(FNB_EPS) * K] : epsm;
-        fc[FA_MUN * TE] = has ? fn[int64_t(FNB_MU) * K] : mum;
+        fc[FA_DETN * TE] = has ? fn[IX(FNB_DET) * K] : det;
+        fc[FA_EPSN * TE] = has ? fn[IX(FNB_EPS) * K] : epsm;
+        fc[FA_MUN * TE] = has ? fn[IX(FNB_MU) * K] : mum;
     };
     if (grp < FACE_GROUPS) {
         face_consts(grp);
@@ -205,15 +206,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
 #pragma unroll
         for (int i = 0; i < BATCH; ++i) {
             const int r = lg + i * LG;
-            tmp[i] = (i < UR && r < 6 * N && active) ? lam[int64_t(r) * C + col] : R(0);
+            tmp[i] = (i < UR && r < 6 * N && active) ? lam[IX(r) * C + col] : R(0);
         }
         if (grp < 24 && active) {   // round-0 item of phase 2: face grp / 6, component grp % 6
-            const int32_t code = prm.nbr[int64_t(grp / 6) * K + e];
-            const int64_t ne = code >> 2;
+            const int32_t code = prm.nbr[IX(grp / 6) * K + e];
+            const IX ne = code >> 2;
             if (code >= 0 && ne < K) {
-                const int64_t ncol = ne * S + s;
+                const IX ncol = ne * S + s;
 #pragma unroll
-                for (int l = 0; l < N; ++l) vn[l] = lam[int64_t((grp % 6) * N + l) * C + ncol];
+                for (int l = 0; l < N; ++l) vn[l] = lam[IX((grp % 6) * N + l) * C + ncol];
                 vn_ready = true;
             }
         }
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
 #pragma unroll
                 for (int i = 0; i < BATCH; ++i) {
                     const int r = lg + (i0 + i) * LG;
-                    tmp[i] = (i0 + i < UR && r < 6 * N && active) ? lam[int64_t(r) * C + col] : R(0);
+                    tmp[i] = (i0 + i < UR && r < 6 * N && active) ? lam[IX(r) * C + col] : R(0);
                 }
             }
 #pragma unroll
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
 #pragma unroll
         for (int i = 0; i < ER; ++i) {
             const int k = lg + i * LG;
-            tmpe[i] = (k < EG && active) ? gr[int64_t(k) * K + e]
+            tmpe[i] = (k < EG && active) ? gr[IX(k) * K + e]
                                          : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
         }
 #pragma unroll
@@ -274,14 +275,14 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
     // ---- 2: traces: own of rho (= gamma), neighbour of lam ------------------------
     for (int r = grp; r < 24; r += NG) {
         const int f = r / 6, comp = r % 6;
-        const int32_t code = active ? prm.nbr[int64_t(f) * K + e] : -1;
-        const int64_t ne = code >> 2;
+        const int32_t code = active ? prm.nbr[IX(f) * K + e] : -1;
+        const IX ne = code >> 2;
         const bool has_nbr = code >= 0 && ne < K;
         if (code >= 0 && ne >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
         if (has_nbr && !(r == grp && vn_ready)) {
-            const int64_t ncol = ne * S + s;
+            const IX ncol = ne * S + s;
 #pragma unroll
-            for (int l = 0; l < N; ++l) vn[l] = lam[int64_t(comp * N + l) * C + ncol];
+            for (int l = 0; l < N; ++l) vn[l] = lam[IX(comp * N + l) * C + ncol];
         }
         R v[N], acc[NF];
 #pragma unroll
@@ -408,8 +409,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
                 R dE[3], dH[3];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    dE[r] = jp[int64_t((f * 6 + r) * NF + m) * C + col];
-                    dH[r] = jp[int64_t((f * 6 + 3 + r) * NF + m) * C + col];
+                    dE[r] = jp[IX((f * 6 + r) * NF + m) * C + col];
+                    dH[r] = jp[IX((f * 6 + 3 + r) * NF + m) * C + col];
                 }
                 R nxdE[3], nnxdE[3], nxdH[3], nnxdH[3];
                 cross3(n, dE, nxdE);
@@ -494,8 +495,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
                     xiR[k] += atj[a] * xi3[a] * ait[3 * a + k];   // row j (forward) for the gradient
                 }
         }
-        const int64_t C2 = int64_t(prm.npml) * S;
-        const int64_t acol = int64_t(pi) * S + s;
+        const IX C2 = IX(prm.npml) * S;
+        const IX acol = IX(pi) * S + s;
         R* lu = static_cast<R*>(prm.lu);
         const R* lra = static_cast<const R*>(prm.lr_aux);
         R* lua = static_cast<R*>(prm.lu_aux);
@@ -507,27 +508,27 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
         for (int l = lo; l < hi; ++l) {
             R w = rh[(comp * N + l) * TE + c];
-            const int64_t gi = int64_t(comp * N + l) * C + col;
+            const IX gi = IX(comp * N + l) * C + col;
             // mass term of the gradient: -(1/mat) rho_c . rhs_c
             gmass += rs[(comp * N + l) * TE + c] * raw[gi];
             if (pi >= 0) {
                 const R l0 = us[((fb + 0) * N + l) * TE + c];
                 const R l1 = us[((fb + 1) * N + l) * TE + c];
                 const R l2 = us[((fb + 2) * N + l) * TE + c];
-                const int64_t ai = int64_t(fb * N + l) * C2 + acol;
-                const R p0 = lra[ai], p1 = lra[ai + int64_t(N) * C2], p2 = lra[ai + 2 * int64_t(N) * C2];
+                const IX ai = IX(fb * N + l) * C2 + acol;
+                const R p0 = lra[ai], p1 = lra[ai + IX(N) * C2], p2 = lra[ai + 2 * IX(N) * C2];
                 w -= etaT[0] * l0 + etaT[1] * l1 + etaT[2] * l2;
                 w += mat * (xiT[0] * p0 + xiT[1] * p1 + xiT[2] * p2);
                 const R lj = j == 0 ? l0 : (j == 1 ? l1 : l2);
                 const R pj = j == 0 ? p0 : (j == 1 ? p1 : p2);
                 const R wa = -lj / mat - (sigT[0] * p0 + sigT[1] * p1 + sigT[2] * p2);
-                const int64_t aj2 = int64_t(comp * N + l) * C2 + acol;
+                const IX aj2 = IX(comp * N + l) * C2 + acol;
                 lua[aj2] += dt * wa;
                 // PML gradient terms: lam_j p_j / mat^2 + lam_aux_j (A^T xi A^-T u)_j
                 const R apj = af[aj2];
-                const R u0 = uf[int64_t((fb + 0) * N + l) * C + col];
-                const R u1 = uf[int64_t((fb + 1) * N + l) * C + col];
-                const R u2 = uf[int64_t((fb + 2) * N + l) * C + col];
+                const R u0 = uf[IX((fb + 0) * N + l) * C + col];
+                const R u1 = uf[IX((fb + 1) * N + l) * C + col];
+                const R u2 = uf[IX((fb + 2) * N + l) * C + col];
                 gpml += lj * apj / (mat * mat) + pj * (xiR[0] * u0 + xiR[1] * u1 + xiR[2] * u2);
             }
             lu[gi] += dt * w;
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
 
     // ---- 6: per-column gradient (one owner thread per column, fixed order) --------
     if (grp == 0 && active) {
-        const double eps = prm.geo[int64_t(G_EPS) * K + e], mu = prm.geo[int64_t(G_MU) * K + e];
+        const double eps = prm.geo[IX(G_EPS) * K + e], mu = prm.geo[IX(G_MU) * K + e];
         const double Z = sqrt(mu / eps);
         double dz = 0.0, ge = 0.0, gm = 0.0;
         for (int i = 0; i < 4 * CH; ++i) dz += zs[i * TE + c];

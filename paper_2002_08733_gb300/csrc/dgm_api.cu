@@ -1174,6 +1174,7 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
                 ap.pml = prm.pml;
                 ap.status = prm.status;
                 ap.grad = gcol;
+                ap.force_index64 = P->force_index64;
                 ap.K = K;
                 ap.npml = P->mesh.npml;
                 ap.S = Sc;

@@ -87,6 +87,7 @@ struct AdjParams {
     const int32_t* pml;
     int32_t* status;
     double* grad;         // [2][K*S]: per-column d/d eps, d/d mu accumulators
+    int32_t force_index64;// 1: 64-bit index arithmetic even where 32 bits suffice
     int64_t K;
     int64_t npml;
     int32_t S;

@@ -36,21 +36,39 @@ constexpr int kNT = sizeof(Real) == 8 ? 192 : 384;
 #ifdef DGM_ADJ
 constexpr int kTEA = sizeof(Real) == 8 ? 16 : 32;
 constexpr int kNTA = sizeof(Real) == 8 ? 192 : 384;
-int launch_adj(const AdjParams& prm, cudaStream_t st) {
+template <typename IX>
+int launch_adj_ix(const AdjParams& prm, unsigned grid, cudaStream_t st) {
     constexpr size_t smem = adjoint_smem_bytes<kP, Real, kTEA, kNTA>();
     static bool configured = false;
-    auto k = adjoint_kernel<kP, Real, kTEA, kNTA>;
+    auto k = adjoint_kernel<kP, Real, kTEA, kNTA, IX>;
     if (!configured) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
             cudaSuccess)
             return DGM_ECUDA;
         configured = true;
     }
+    k<<<grid, kNTA, smem, st>>>(prm);
+    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+}
+
+// true when every index the adjoint kernel forms is below 2^32: field rows
+// (6N x C), face jumps (24 NF x C), auxiliaries, geometry, the per-face
+// table, neighbours and the two gradient rows (2C)
+bool fits_32bit(const AdjParams& p) {
+    const uint64_t lim = uint64_t(1) << 32;
+    const uint64_t K = uint64_t(p.K), C = K * uint64_t(p.S);
+    const uint64_t N = uint64_t(nmodes(kP)), NF = uint64_t(nfmodes(kP));
+    return 6 * N * C < lim && 24 * NF * C < lim && 6 * N * uint64_t(p.npml) * uint64_t(p.S) < lim &&
+           uint64_t(G_COUNT) * K < lim && 4 * uint64_t(FNB_COUNT) * K < lim && 4 * K < lim &&
+           2 * C < lim;
+}
+
+int launch_adj(const AdjParams& prm, cudaStream_t st) {
     const int64_t C = prm.K * prm.S;
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + kTEA - 1) / kTEA);
-    k<<<grid, kNTA, smem, st>>>(prm);
-    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+    return (!prm.force_index64 && fits_32bit(prm)) ? launch_adj_ix<uint32_t>(prm, grid, st)
+                                                    : launch_adj_ix<int64_t>(prm, grid, st);
 }
 #elif defined(DGM_PAIR)
 // paired kernel: 64 columns per CTA, two per thread (LSRK stages only)
