@@ -47,6 +47,19 @@ KERNEL_NAMES = ["stage_kernel<3,float,32,384,LSRK>", "stage_kernel<3,float,32,19
 UNIT = "DoF-updates/s"
 
 
+def kernel_name(variant, K, N, S):
+    """The stage kernel a variant launches; single-column shapes use 32-bit index
+    arithmetic when every index fits (the library's own test: field and
+    face-jump rows x columns, geometry, per-face table below 2^32)."""
+    name = KERNEL_NAMES[variant]
+    if variant < 3:
+        NF = {4: 3, 10: 6, 20: 10, 35: 15, 56: 21}[N]
+        C = K * S
+        fits = max(6 * N * C, 24 * NF * C, 16 * K, 52 * K) < 2 ** 32
+        name = name[:-1] + (",unsigned int>" if fits else ",long>")
+    return name
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -535,7 +548,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": peak_src,
-                     "kernel": KERNEL_NAMES[chosen],
+                     "kernel": kernel_name(chosen, r32["K"], r32["N"], r32["S"]),
                      "algorithmic_bytes_per_launch": bytes_step / 5},
         "fp64": {"value": r64["value"], "ms_per_step": r64["ms"] / r64["steps"],
                  "steps": r64["steps"], "dtype": "f64"},
