@@ -72,17 +72,32 @@ int launch_adj(const AdjParams& prm, cudaStream_t st) {
 }
 #elif defined(DGM_PAIR)
 // paired kernel: 64 columns per CTA, two per thread (LSRK stages only)
-int launch_mode(const StageParams& prm, cudaStream_t st) {
+template <typename IX>
+int launch_pair_ix(const StageParams& q, unsigned grid, cudaStream_t st) {
     using Pair = DGM_PAIR;
     constexpr size_t smem = stage2_smem_bytes<kP, Pair>();
     static bool configured = false;
-    auto k = stage2_kernel<kP, Pair, kNT>;
+    auto k = stage2_kernel<kP, Pair, kNT, IX>;
     if (!configured) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
             cudaSuccess)
             return DGM_ECUDA;
         configured = true;
     }
+    k<<<grid, kNT, smem, st>>>(q);
+    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+}
+
+// every index below 2^32 (the same buffers as the single-column kernel)
+bool fits_32bit(const StageParams& p) {
+    const uint64_t lim = uint64_t(1) << 32;
+    const uint64_t K = uint64_t(p.K), C = K * uint64_t(p.S);
+    const uint64_t N = uint64_t(nmodes(kP));
+    return 6 * N * C + 64 < lim && 6 * N * uint64_t(p.npml) * uint64_t(p.S) < lim &&
+           uint64_t(G_COUNT) * K < lim && 4 * uint64_t(FNB_COUNT) * K < lim && 4 * K < lim;
+}
+
+int launch_mode(const StageParams& prm, cudaStream_t st) {
     const int64_t C = prm.K * prm.S;
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + 63) / 64);
@@ -90,8 +105,8 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     q.dt_f = float(prm.dt);
     q.a_f = float(prm.a);
     q.b_f = float(prm.b);
-    k<<<grid, kNT, smem, st>>>(q);
-    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+    return (!q.force_index64 && fits_32bit(q)) ? launch_pair_ix<uint32_t>(q, grid, st)
+                                               : launch_pair_ix<int64_t>(q, grid, st);
 }
 #else
 template <typename IX>

@@ -62,7 +62,7 @@ __host__ __device__ constexpr size_t stage2_smem_bytes() {
            sizeof(int2) * 4 * 32;
 }
 
-template <int P, typename PR, int NT>
+template <int P, typename PR, int NT, typename IX = int64_t>
 __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
     constexpr int TE = 32;
     constexpr int N = nmodes(P);
@@ -80,37 +80,37 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
 
     const int c = threadIdx.x % TE;
     const int grp = threadIdx.x / TE;
-    const int64_t K = prm.K;
+    const IX K = prm.K;
     const int S = prm.S;
-    const int64_t C = K * S;
-    const int64_t colA = int64_t(blockIdx.x) * 64 + c, colB = colA + 32;
+    const IX C = K * S;
+    const IX colA = IX(blockIdx.x) * 64 + c, colB = colA + 32;
     const bool actA = colA < C, actB = colB < C;
-    const int64_t eA = actA ? colA / S : 0, eB = actB ? colB / S : 0;
+    const IX eA = actA ? colA / S : 0, eB = actB ? colB / S : 0;
     const int sA = actA ? int(colA - eA * S) : 0, sB = actB ? int(colB - eB * S) : 0;
     const float* u = static_cast<const float*>(prm.u);
     const float* gr = static_cast<const float*>(prm.geo_r);
     if (grp < 4)
-        nbs[grp * TE + c] = make_int2(actA ? prm.nbr[int64_t(grp) * K + eA] : -1,
-                                      actB ? prm.nbr[int64_t(grp) * K + eB] : -1);
+        nbs[grp * TE + c] = make_int2(actA ? prm.nbr[IX(grp) * K + eA] : -1,
+                                      actB ? prm.nbr[IX(grp) * K + eB] : -1);
 
     // ---- phase 1 -------------------------------------------------------------------
     auto geo2 = [&](int k, float dflt) {
-        return PR(actA ? gr[int64_t(k) * K + eA] : dflt, actB ? gr[int64_t(k) * K + eB] : dflt);
+        return PR(actA ? gr[IX(k) * K + eA] : dflt, actB ? gr[IX(k) * K + eB] : dflt);
     };
     constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
     if (grp < FACE_GROUPS) {
         const int f = grp;
-        const float* fn = static_cast<const float*>(prm.fnb_r) + int64_t(f * FNB_COUNT) * K;
-        const int32_t ca = actA ? prm.nbr[int64_t(f) * K + eA] : -1;
-        const int32_t cb = actB ? prm.nbr[int64_t(f) * K + eB] : -1;
+        const float* fn = static_cast<const float*>(prm.fnb_r) + IX(f * FNB_COUNT) * K;
+        const int32_t ca = actA ? prm.nbr[IX(f) * K + eA] : -1;
+        const int32_t cb = actB ? prm.nbr[IX(f) * K + eB] : -1;
         PR ait[9], aitn[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) ait[k] = geo2(G_AIT + k, k % 4 == 0 ? 1.f : 0.f);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-            aitn[k] = PR(actA ? fn[int64_t(FNB_AIT + k) * K + eA] : ait[k].a(),
-                         actB ? fn[int64_t(FNB_AIT + k) * K + eB] : ait[k].b());
-        const PR zn(actA ? fn[int64_t(FNB_Z) * K + eA] : 1.f, actB ? fn[int64_t(FNB_Z) * K + eB] : 1.f);
+            aitn[k] = PR(actA ? fn[IX(FNB_AIT + k) * K + eA] : ait[k].a(),
+                         actB ? fn[IX(FNB_AIT + k) * K + eB] : ait[k].b());
+        const PR zn(actA ? fn[IX(FNB_Z) * K + eA] : 1.f, actB ? fn[IX(FNB_Z) * K + eB] : 1.f);
         face_constants2<PR>(f, ait, geo2(G_DET, 1.f), geo2(G_EPS, 1.f), geo2(G_MU, 1.f),
                             ca >= 0 && (ca >> 2) < K, cb >= 0 && (cb >> 2) < K, aitn, zn, prm.upwind,
                             fg + f * FG * TE + c);
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
             for (int i = 0; i < BATCH; ++i) {
                 const int r = lg + (i0 + i) * LG;
                 const bool ok = i0 + i < UR && r < 6 * N;
-                tmp[i] = PR(ok && actA ? u[int64_t(r) * C + colA] : 0.f, ok && actB ? u[int64_t(r) * C + colB] : 0.f);
+                tmp[i] = PR(ok && actA ? u[IX(r) * C + colA] : 0.f, ok && actB ? u[IX(r) * C + colB] : 0.f);
             }
 #pragma unroll
             for (int i = 0; i < BATCH; ++i) {
@@ -162,12 +162,12 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
                 atomicOr(prm.status, ST_BAD_NEIGHBOUR);
             PR vn[N];
             if (hA || hB) {
-                const int64_t na = hA ? (int64_t(code.x >> 2) * S + sA) : 0;
-                const int64_t nb = hB ? (int64_t(code.y >> 2) * S + sB) : 0;
+                const IX na = hA ? (IX(code.x >> 2) * S + sA) : 0;
+                const IX nb = hB ? (IX(code.y >> 2) * S + sB) : 0;
 #pragma unroll
                 for (int l = 0; l < N; ++l)
-                    vn[l] = PR(hA ? u[int64_t(ncomp * N + l) * C + na] : 0.f,
-                               hB ? u[int64_t(ncomp * N + l) * C + nb] : 0.f);
+                    vn[l] = PR(hA ? u[IX(ncomp * N + l) * C + na] : 0.f,
+                               hB ? u[IX(ncomp * N + l) * C + nb] : 0.f);
             }
             if (ni < NOWN) {
                 const int ocomp = ni % 6, fp = ni / 6;
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
 #pragma unroll
         for (int i = 0; i < RPF; ++i)
             if (lo + i < hi)
-                resv[i] = PR(actA ? resg[int64_t(comp * N + lo + i) * C + colA] : 0.f,
-                             actB ? resg[int64_t(comp * N + lo + i) * C + colB] : 0.f);
+                resv[i] = PR(actA ? resg[IX(comp * N + lo + i) * C + colA] : 0.f,
+                             actB ? resg[IX(comp * N + lo + i) * C + colB] : 0.f);
     }
     for (int it = grp; it < 6 * NPART; it += NG) {
         const int comp = it / NPART;
@@ -301,9 +301,9 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
         rhs_part<P, PR, TE, NPART>(part, comp, c, us, trO, sgn, acc);
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
         if (comp < 3 && prm.src != nullptr) {
-            const double* ra = prm.src + int64_t(sA) * (SRC_HDR + 3 * N);
-            const double* rb = prm.src + int64_t(sB) * (SRC_HDR + 3 * N);
-            const bool hitA = actA && int64_t(ra[0]) == eA, hitB = actB && int64_t(rb[0]) == eB;
+            const double* ra = prm.src + IX(sA) * (SRC_HDR + 3 * N);
+            const double* rb = prm.src + IX(sB) * (SRC_HDR + 3 * N);
+            const bool hitA = actA && ra[0] >= 0.0 && IX(ra[0]) == eA, hitB = actB && rb[0] >= 0.0 && IX(rb[0]) == eB;
             if (hitA || hitB) {
                 const double tt = prm.tdev ? *prm.tdev + prm.t : prm.t;
                 const float ga = hitA ? float(source_time(tt, ra[1], ra[2], ra[3])) : 0.f;
@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
                 xi_row[k] = psel(piA >= 0, piB >= 0, xi_row[k], PR(0.0));
             }
         }
-        const int64_t C2 = int64_t(prm.npml) * S;
-        const int64_t acA = int64_t(piA) * S + sA, acB = int64_t(piB) * S + sB;
+        const IX C2 = IX(prm.npml) * S;
+        const IX acA = IX(piA) * S + sA, acB = IX(piB) * S + sB;
         float* uo = static_cast<float*>(prm.u_out);
         float* res = static_cast<float*>(prm.res);
         const float* aux = static_cast<const float*>(prm.aux);
@@ -398,13 +398,13 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
             const PR r2 = rh[((fb + 2) * N + l) * TE + c];
             PR du = brow[0] * r0 + brow[1] * r1 + brow[2] * r2;
             const PR uv = us[(comp * N + l) * TE + c];
-            const int64_t row = int64_t(comp * N + l) * C;
+            const IX row = IX(comp * N + l) * C;
             if (any_pml) {
                 const PR u0 = us[((fb + 0) * N + l) * TE + c];
                 const PR u1 = us[((fb + 1) * N + l) * TE + c];
                 const PR u2 = us[((fb + 2) * N + l) * TE + c];
                 auto ld = [&](int cc) {
-                    const int64_t rw = int64_t(cc * N + l) * C2;
+                    const IX rw = IX(cc * N + l) * C2;
                     return PR(piA >= 0 ? aux[rw + acA] : 0.f, piB >= 0 ? aux[rw + acB] : 0.f);
                 };
                 const PR a0 = ld(fb), a1 = ld(fb + 1), a2 = ld(fb + 2);
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
                 du = du - (eta_row[0] * u0 + eta_row[1] * u1 + eta_row[2] * u2 + av * prcp(mat));
                 const PR da = mat * (xi_row[0] * u0 + xi_row[1] * u1 + xi_row[2] * u2) -
                               (sig_row[0] * a0 + sig_row[1] * a1 + sig_row[2] * a2);
-                const int64_t rw = int64_t(comp * N + l) * C2;
+                const IX rw = IX(comp * N + l) * C2;
                 if (piA >= 0) {
                     const float rr = (ca == 0.f ? 0.f : ca * auxr[rw + acA]) + prm.dt_f * da.a();
                     auxr[rw + acA] = rr;
