@@ -76,7 +76,7 @@ def test_quad_points_lie_in_their_elements(lib):
 
 
 @pytest.mark.parametrize("case", ["repeated", "range", "degenerate", "nonmanifold",
-                                  "eps", "order", "leapfrog_upwind", "dt", "columns"])
+                                  "eps", "order", "leapfrog_upwind", "dt", "columns", "empty"])
 def test_invalid_inputs_are_rejected(lib, case):
     from paper_2002_08733_gb300 import dgmax as D
     xyz, tets = W.kuhn_mesh(2)
@@ -104,8 +104,11 @@ def test_invalid_inputs_are_rejected(lib, case):
         kw["dt"] = 0.0
     elif case == "columns":
         kw["S"] = 0
+    elif case == "empty":
+        tets = tets[:0]
+        kw["eps"] = kw["mu"] = 1.0
     with pytest.raises(expect) as ei:
         D.Plan(xyz, tets, kw.pop("eps"), kw.pop("mu"), kw.pop("p"), **kw)
     codes = {"repeated": 2, "range": 2, "degenerate": 2, "nonmanifold": 2, "eps": 1,
-             "order": 3, "leapfrog_upwind": 3, "dt": 1, "columns": 1}
+             "order": 3, "leapfrog_upwind": 3, "dt": 1, "columns": 1, "empty": 1}
     assert ei.value.code == codes[case]
