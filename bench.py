@@ -190,7 +190,7 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     elif precision == "fp32":
         v, ms = g.autotune()
         tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms],
-                 "variants": VARIANT_NAMES[:len(ms)]}
+                 "variants": VARIANT_NAMES[:len(ms)], "tile_groups": g.tile_groups()}
     t = 0.0
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -240,7 +240,8 @@ def run_pml(precision, steps, warmup, n=40):
     tuned = None
     if precision == "fp32":   # the plan's own tile-shape choice (state untouched)
         v, ms_v = g.autotune()
-        tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms_v]}
+        tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms_v],
+                 "tile_groups": g.tile_groups()}
     t = 0.0
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -367,6 +368,7 @@ def run_adjoint(steps):
                  device=dev, S=w.S, pml=w.pml, max_receivers=len(rec))
     g.set_sources(w.extra["sources"])
     g.set_receivers(rec)
+    g.autotune()              # tile shape and tile order for the forward stages
     mu = torch.ones(g.K, dtype=torch.float64)
     with torch.no_grad():
         target = D.receiver_records(g, torch.tensor(w.extra["eps_target"]), mu, steps)

@@ -204,7 +204,8 @@ int dgm_adjoint(dgm_plan* plan, int64_t n_steps, double t0, const double* drecor
 
 /* Autotuner: times each compiled tile shape (columns per CTA x threads per
  * CTA) of the LSRK4 stage kernel on the plan's current state, `reps` launches
- * each, and keeps the fastest for later dgm_advance / dgm_batch_create calls.
+ * each, and keeps the fastest for later dgm_advance / dgm_batch_create calls;
+ * then times the tile visiting orders of dgm_set_tile_groups for that shape.
  * The plan's state is not modified: outputs go to `workspace`, device memory
  * of 2*align256(bytes_fields) + 2*align256(bytes_aux) bytes.  ms_out (host,
  * may be NULL) receives the mean time per launch of each variant.
@@ -220,6 +221,15 @@ int dgm_set_variant(dgm_plan* plan, int32_t variant);
  * always, to check that path on problems of any size.  Results are the same
  * either way.  DGM_EINVAL for other values. */
 int dgm_set_index64(dgm_plan* plan, int32_t force);
+/* Order in which the stage and adjoint kernels visit their column tiles:
+ * with groups = G > 1 (and a tile count that G divides) consecutive CTAs
+ * take tiles from G equal segments of the columns in turn, which keeps the
+ * neighbours' coefficients of meshes numbered in G blocks (e.g. a Kuhn grid
+ * numbered by tetrahedron type) in L2; 1 = plain order.  Results do not
+ * depend on it.  dgm_autotune picks it after the tile shape (candidates 1,
+ * 2, 3, 4, 6, 8, 12); DGM_EINVAL outside 1..64. */
+int dgm_set_tile_groups(dgm_plan* plan, int32_t groups);
+int dgm_get_tile_groups(const dgm_plan* plan, int32_t* groups);
 
 /* Index (0 or 1) of the bound field/aux buffer that holds the current state. */
 int dgm_current(const dgm_plan* plan);

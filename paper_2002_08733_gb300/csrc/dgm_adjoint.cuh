@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
     const IX K = prm.K;
     const int S = prm.S;
     const IX C = K * S;
-    const IX col = IX(blockIdx.x) * TE + c;
+    const IX col = IX(tile_index(prm.tile_groups)) * TE + c;
     const bool active = col < C;
     const IX e = active ? col / S : 0;
     const int s = active ? int(col - e * S) : 0;

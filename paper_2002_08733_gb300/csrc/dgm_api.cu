@@ -81,6 +81,7 @@ struct dgm_plan {
     int device = -1;
     int variant = 0;          // LSRK stage tile shape chosen by dgm_autotune
     int force_index64 = 0;    // dgm_set_index64
+    int tile_groups = 1;      // tile visiting order (dgm_autotune, dgm_set_tile_groups)
     float variant_ms[8] = {0};
 };
 
@@ -384,6 +385,7 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.dt = P->opt.dt;
     prm.variant = P->variant;
     prm.force_index64 = P->force_index64;
+    prm.tile_groups = P->tile_groups;
 }
 
 int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double* pos,
@@ -1175,6 +1177,7 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
                 ap.status = prm.status;
                 ap.grad = gcol;
                 ap.force_index64 = P->force_index64;
+                ap.tile_groups = P->tile_groups;
                 ap.K = K;
                 ap.npml = P->mesh.npml;
                 ap.S = Sc;
@@ -1216,28 +1219,26 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = 0;
-    float best_ms = 1e30f;
-    for (int v = 0; v < P->kt->n_variants; ++v) {
-        prm.variant = v;
-        int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);   // warm
-        if (rc) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return fail(rc, "stage kernel launch failed");
-        }
+    // mean time of `n` launches of the current prm (after one warm launch)
+    auto time_it = [&](int n, float* ms) -> int {
+        int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+        if (rc) return fail(rc, "stage kernel launch failed");
         cudaEventRecord(e0, P->stream);
-        for (int r = 0; r < reps; ++r) P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+        for (int r = 0; r < n; ++r) P->kt->launch_stage(prm, MODE_LSRK, P->stream);
         cudaEventRecord(e1, P->stream);
         cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_fail(e, "autotune timing");
-        }
+        if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+        cudaEventElapsedTime(ms, e0, e1);
+        *ms /= n;
+        return DGM_OK;
+    };
+    int best = 0, rc = DGM_OK;
+    float best_ms = 1e30f;
+    prm.tile_groups = 1;
+    for (int v = 0; v < P->kt->n_variants && rc == DGM_OK; ++v) {
+        prm.variant = v;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
+        if ((rc = time_it(reps, &ms)) != DGM_OK) break;
         if (v < 8) P->variant_ms[v] = ms;
         if (ms_out) ms_out[v] = ms;
         if (ms < best_ms) {
@@ -1245,9 +1246,43 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
             best = v;
         }
     }
+    // then the tile visiting order of the chosen shape (1 = in order)
+    int best_g = 1;
+    if (rc == DGM_OK) {
+        prm.variant = best;
+        const int cand[] = {1, 2, 3, 4, 6, 8, 12};
+        float g_ms[7] = {0};
+        for (int i = 0; i < 7 && rc == DGM_OK; ++i) {
+            prm.tile_groups = cand[i];
+            rc = time_it(reps < 5 ? 5 : reps, &g_ms[i]);
+        }
+        if (rc == DGM_OK) {
+            float bms = g_ms[0];
+            for (int i = 1; i < 7; ++i)
+                if (g_ms[i] < 0.99f * bms) {   // only a clear gain moves off the plain order
+                    bms = g_ms[i];
+                    best_g = cand[i];
+                }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc != DGM_OK) return rc;
     P->variant = best;
+    P->tile_groups = best_g;
+    return DGM_OK;
+}
+
+extern "C" int dgm_set_tile_groups(dgm_plan* P, int32_t groups) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (groups < 1 || groups > 64) return fail(DGM_EINVAL, "tile groups must be 1..64");
+    P->tile_groups = groups;
+    return DGM_OK;
+}
+
+extern "C" int dgm_get_tile_groups(const dgm_plan* P, int32_t* groups) {
+    if (!P || !groups) return fail(DGM_EINVAL, "null argument");
+    *groups = P->tile_groups;
     return DGM_OK;
 }
 

@@ -67,6 +67,7 @@ struct StageParams {
     void* jumps;          // MODE_RAW: physical face jumps dE, dH [4][6][NF][K][S]
     int32_t variant;      // tile-shape variant of the LSRK stage kernel (autotuner)
     int32_t force_index64;// 1: 64-bit index arithmetic even where 32 bits suffice
+    int32_t tile_groups;  // tile visiting order: G interleaved segments (1: in order)
 };
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms
@@ -88,6 +89,7 @@ struct AdjParams {
     int32_t* status;
     double* grad;         // [2][K*S]: per-column d/d eps, d/d mu accumulators
     int32_t force_index64;// 1: 64-bit index arithmetic even where 32 bits suffice
+    int32_t tile_groups;  // tile visiting order (as in StageParams)
     int64_t K;
     int64_t npml;
     int32_t S;

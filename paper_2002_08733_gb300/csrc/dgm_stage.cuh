@@ -45,6 +45,19 @@
 
 namespace dgm {
 
+// Tile visited by this CTA.  With G > 1 groups (and a grid that G divides)
+// CTAs b = 0, 1, 2, ... take tiles from G equal segments in turn, so that
+// tiles far apart in the column numbering run at the same time: meshes whose
+// neighbours are numbered in G blocks (a Kuhn grid numbered type by type has
+// its face neighbours in other type blocks) then find their neighbours'
+// coefficients in L2.  Any order gives the same results.
+__device__ __forceinline__ unsigned tile_index(int groups) {
+    const unsigned b = blockIdx.x, n = gridDim.x;
+    if (groups <= 1 || n % unsigned(groups) != 0) return b;
+    const unsigned g = unsigned(groups);
+    return (b % g) * (n / g) + b / g;
+}
+
 // offset of the first mode of total degree d (3-D) and (2-D)
 __host__ __device__ constexpr int off3(int d) { return d <= 0 ? 0 : nmodes(d - 1); }
 __host__ __device__ constexpr int off2(int d) { return d <= 0 ? 0 : nfmodes(d - 1); }
@@ -269,7 +282,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     const IX K = prm.K;
     const int S = prm.S;
     const IX C = K * S;
-    const IX col = IX(blockIdx.x) * TE + c;
+    const IX col = IX(tile_index(prm.tile_groups)) * TE + c;
     const bool active = col < C;
     const IX e = active ? col / S : 0;
     const int s = active ? int(col - e * S) : 0;

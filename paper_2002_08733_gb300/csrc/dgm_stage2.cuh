@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
     const IX K = prm.K;
     const int S = prm.S;
     const IX C = K * S;
-    const IX colA = IX(blockIdx.x) * 64 + c, colB = colA + 32;
+    const IX colA = IX(tile_index(prm.tile_groups)) * 64 + c, colB = colA + 32;
     const bool actA = colA < C, actB = colB < C;
     const IX eA = actA ? colA / S : 0, eB = actB ? colB / S : 0;
     const int sA = actA ? int(colA - eA * S) : 0, sB = actB ? int(colB - eB * S) : 0;

@@ -76,6 +76,8 @@ _SIGS = {
     "dgm_autotune_info": [_P, _P, _P],
     "dgm_set_variant": [_P, ctypes.c_int32],
     "dgm_set_index64": [_P, ctypes.c_int32],
+    "dgm_set_tile_groups": [_P, ctypes.c_int32],
+    "dgm_get_tile_groups": [_P, ctypes.c_void_p],
     "dgm_adjoint_workspace": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
     "dgm_forward_record": [_P, ctypes.c_int64, ctypes.c_double, _P, _P],
     "dgm_adjoint": [_P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P],
@@ -325,6 +327,15 @@ class Solver(Plan):
 
     def set_variant(self, v):
         _check(_lib.dgm_set_variant(self.handle, int(v)))
+
+    def set_tile_groups(self, groups):
+        """Tile visiting order of the stage kernels (1: plain order)."""
+        _check(_lib.dgm_set_tile_groups(self.handle, int(groups)))
+
+    def tile_groups(self):
+        g = ctypes.c_int32()
+        _check(_lib.dgm_get_tile_groups(self.handle, ctypes.byref(g)))
+        return g.value
 
     def set_index64(self, force=True):
         """Force 64-bit index arithmetic in the stage kernels (default: automatic)."""

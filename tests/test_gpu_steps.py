@@ -99,6 +99,36 @@ def test_index_width_paths(D, prec, tol, S):
     assert rel_l2(got[0][1], ref_aux[g.pml_elements()]) < tol
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tile_order_does_not_change_results(D, prec):
+    """The tile visiting order (dgm_set_tile_groups) is a scheduling choice:
+    plain order, interleaved groups that divide the tile count and a count
+    that does not (plain order then) give bit-identical LSRK4 steps with PML
+    and a source; the autotuner's choice is one of its candidates."""
+    xyz, tets = W.kuhn_mesh(4, (-1, -1, -1), (1, 1, 1), jitter=0.1, seed=27)
+    K, p, S = len(tets), 2, 2
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+    srcs = [W.dipole((0.11, -0.07, 0.05), 2.0, 1.0), None]
+    dt = W.stable_dt(0.5, p)
+    u = W.random_state(K, S, p, seed=28) * 1e-2
+    got = []
+    for groups in (1, 2, 6, 8, 5):
+        g = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", dt, S=S, pml=pml)
+        g.set_tile_groups(groups)
+        assert g.tile_groups() == groups
+        g.set_sources(srcs)
+        g.set_state(u)
+        g.advance(4, 0.0)
+        got.append((g.state(), g.from_device(g.aux[g.current()])))
+    for st, ax in got[1:]:
+        assert np.array_equal(st, got[0][0]) and np.array_equal(ax, got[0][1])
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", dt, S=S, pml=pml)
+    g.autotune()
+    assert g.tile_groups() in (1, 2, 3, 4, 6, 8, 12)
+    with pytest.raises(D.DgmError):
+        g.set_tile_groups(0)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_lsrk4_pml_dipole_trajectory(D, prec, tol):
     xyz, tets = W.kuhn_mesh(4, (-1, -1, -1), (1, 1, 1))
