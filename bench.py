@@ -186,7 +186,9 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     tuned = None
     if precision == "fp32" and args.variant is not None:
         g.set_variant(args.variant)
-        tuned = {"variant": int(args.variant), "forced": True}
+        if args.tile_groups is not None:
+            g.set_tile_groups(args.tile_groups)
+        tuned = {"variant": int(args.variant), "forced": True, "tile_groups": g.tile_groups()}
     elif precision == "fp32":
         v, ms = g.autotune()
         tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms],
@@ -462,6 +464,8 @@ def main():
     ap.add_argument("--variant", type=int, default=None,
                     help="force the FP32 stage-kernel tile shape instead of autotuning "
                          "(profiling runs: the autotuner's timings are distorted under ncu)")
+    ap.add_argument("--tile-groups", type=int, default=None,
+                    help="with --variant: force the FP32 tile visiting order (default: plain order)")
     ap.add_argument("--adjoint-steps", type=int, default=60)
     ap.add_argument("--pml-steps", type=int, default=20)
     args = ap.parse_args()
@@ -539,8 +543,10 @@ def main():
         txt = open(tfile).read()
         m = re.search(r"traffic_bytes_per_element_stage:\s*(\d+)", txt)
         mv = re.search(r"profiled_variant:\s*(\d+)", txt)
-        # counters of another kernel variant say nothing about this one
-        if m and mv and int(mv.group(1)) == chosen:
+        mg = re.search(r"profiled_tile_groups:\s*(\d+)", txt)
+        groups = (r32["tuned"] or {}).get("tile_groups", 1)
+        # counters of another kernel variant or tile order say nothing about this one
+        if m and mv and mg and int(mv.group(1)) == chosen and int(mg.group(1)) == groups:
             traffic = int(m.group(1)) * r32["K"] * r32["S"]
     line = {
         "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
