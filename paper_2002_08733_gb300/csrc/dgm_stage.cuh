@@ -97,18 +97,6 @@ __device__ __forceinline__ void trace_any(int f, const R (&v)[nmodes(P)], R (&ac
     }
 }
 
-// acc[l] += sign * sum_m S[a][l][m] v[m]
-template <int P, typename R, int A>
-__device__ __forceinline__ void deriv_acc(const R* vs, int stride, R sign, R (&acc)[nmodes(P)]) {
-    DerivOp<P, A>::template apply<R>(vs, stride, sign, acc);
-}
-
-// acc[l] += sum_m R[f][m][l] g[m]
-template <int P, typename R, int F>
-__device__ __forceinline__ void lift_face(const R* gs, int stride, R (&acc)[nmodes(P)]) {
-    LiftOp<P, F>::template apply<R>(gs, stride, acc);
-}
-
 template <typename R>
 __device__ __forceinline__ void cross3(const R a[3], const R b[3], R o[3]) {
     o[0] = a[1] * b[2] - a[2] * b[1];
@@ -127,53 +115,9 @@ __device__ __forceinline__ double source_time(double t, double f0, double bw, do
 // Face constants of face f of one element (written to fc[k * TE]): unit outward
 // normal, the neighbour's A^-T (own on a PEC face), flux coefficients, 2|F|,
 // PEC flag.  2|F| n = |det A| A^-T m_f with m_f = 2|F_hat| n_hat of the
-// reference face: (1,1,1), (-1,0,0), (0,-1,0), (0,0,-1).
-template <typename R, int TE>
-__device__ __forceinline__ void face_constants(int f, const R (&ait)[9], R det, R epsm, R mum,
-                                               bool active, const int32_t* __restrict__ nbr,
-                                               const R* __restrict__ gr, int64_t K, int upwind,
-                                               int64_t e, R* fc) {
-    const R m0 = R(f == 0 ? 1 : (f == 1 ? -1 : 0));
-    const R m1 = R(f == 0 ? 1 : (f == 2 ? -1 : 0));
-    const R m2 = R(f == 0 ? 1 : (f == 3 ? -1 : 0));
-    R vn[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) vn[r] = ait[3 * r + 0] * m0 + ait[3 * r + 1] * m1 + ait[3 * r + 2] * m2;
-    const R fs = sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
-#pragma unroll
-    for (int r = 0; r < 3; ++r) fc[(FC_N + r) * TE] = vn[r] / fs;
-    fc[FC_TWOF * TE] = fabs(det) * fs;
-    const R zm = sqrt(mum / epsm);
-    const int32_t code = active ? nbr[int64_t(f) * K + e] : -1;
-    R zp = zm;
-    if (code >= 0 && (code >> 2) < K) {
-        const int64_t ne = code >> 2;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = gr[int64_t(G_AIT + k) * K + ne];
-        zp = sqrt(gr[int64_t(G_MU) * K + ne] / gr[int64_t(G_EPS) * K + ne]);
-        fc[FC_BND * TE] = R(0);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) fc[(FC_AITN + k) * TE] = ait[k];
-        fc[FC_BND * TE] = R(1);
-    }
-    if (upwind) {
-        const R ym = R(1) / zm, yp = R(1) / zp;
-        fc[FC_CE * TE] = zp / (zm + zp);
-        fc[FC_BE * TE] = R(1) / (zm + zp);
-        fc[FC_CH * TE] = yp / (ym + yp);
-        fc[FC_BH * TE] = R(1) / (ym + yp);
-    } else {
-        fc[FC_CE * TE] = R(0.5);
-        fc[FC_BE * TE] = R(0);
-        fc[FC_CH * TE] = R(0.5);
-        fc[FC_BH * TE] = R(0);
-    }
-}
-
-// The same face constants from the per-face neighbour table (neighbour's
-// A^-T and impedance, own values on a boundary face) instead of a gather of
-// the neighbour's geometry: every input is one coalesced load.
+// reference face: (1,1,1), (-1,0,0), (0,-1,0), (0,0,-1).  The neighbour's A^-T
+// and impedance come from the per-face neighbour table (own values on a
+// boundary face), so every input is one coalesced load.
 template <typename R, int TE>
 __device__ __forceinline__ void face_constants_tab(int f, const R (&ait)[9], R det, R epsm, R mum,
                                                    bool has_nbr, const R (&aitn)[9], R zn,
