@@ -357,12 +357,13 @@ def run_cavity():
                 e_rel_coeff_diff_vs_projected_closed_form=err)
 
 
-def run_adjoint(steps):
+def run_adjoint(steps, n=24):
     """Inverse-problem workload: forward with receiver records plus the
-    hand-written adjoint (sqrt(N) checkpointing), FP32 state, FP64 gradient."""
+    hand-written adjoint (sqrt(N) checkpointing), FP32 state, FP64 gradient
+    (n^3 Kuhn grid; 24 is the benchmarked size, smaller for profiling)."""
     import torch
     from paper_2002_08733_gb300 import dgmax as D
-    w = W.inverse_problem(steps=steps)
+    w = W.inverse_problem(steps=steps, n=n)
     xyz, tets = w.mesh()
     dev = torch.device("cuda", 0)
     rec = w.extra["receivers"]
@@ -455,8 +456,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=32,
                     help="Kuhn grid size (32 = the benchmarked workload; smaller for profiling)")
-    ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
-                    help="profile one precision only")
+    ap.add_argument("--only", choices=["fp32", "fp64", "adjoint"], default=None,
+                    help="profile one precision (or the inverse-problem leg) only")
+    ap.add_argument("--adjoint-n", type=int, default=24,
+                    help="Kuhn grid size of the inverse problem (24 = the benchmarked workload)")
     ap.add_argument("--no-pml", action="store_true", help="skip the p=4 dipole-in-PML workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
     ap.add_argument("--batched-steps", type=int, default=10)
@@ -512,6 +515,11 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
+    if args.only == "adjoint":
+        r = run_adjoint(args.adjoint_steps, args.adjoint_n)
+        if rank == 0:
+            print(json.dumps({"profile_run": "adjoint", **r}))
+        return
     if args.only == "fp64":
         r = run_gpu(args, "fp64", args.steps, args.warmup, world, rank)
         if rank == 0:
@@ -588,7 +596,7 @@ def main():
         line["adjoint"] = dict(workload="24^3 PML mesh (82944 tets), p=3, 8 dipoles, 32 "
                                         "receivers, lognormal eps, receiver-misfit loss; FP32 "
                                         "state, FP64 gradient, sqrt(N) checkpoints",
-                               **run_adjoint(args.adjoint_steps))
+                               **run_adjoint(args.adjoint_steps, args.adjoint_n))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, _ = cpu_reference(seconds_budget=15.0)
         line["cpu_baseline"] = base
