@@ -319,6 +319,57 @@ def run_batched(steps, warmup):
                 graph_launches=steps // 2)
 
 
+def run_reflection(n=16, p=4, chunks=8, T=2.4, sigma_max=40.0):
+    """PML reflection (the dipole workload's PML: 0.25 thick, quadratic,
+    sigma_max 40) on a coarser grid: [-1,1]^3 with the PML against the same
+    problem on [-2,2]^3 at the same h, whose own boundary is too far away to be
+    seen in the inner box before T.  Both grids are Kuhn grids numbered type by
+    type, so an element of the small grid is the element of the large one with
+    the same type and a shifted cube.  Reflection = max over sampled times of
+    the E-coefficient difference in the small grid's inner box [-0.75, 0.75]^3,
+    relative to the max over the same times of the large grid's E there.  FP32.
+    sigma_max sets the small grid's PML only (0: its walls reflect fully)."""
+    import torch
+    from paper_2002_08733_gb300 import dgmax as D
+    ws = W.dipole_pml(n=n, p=p, sigma_max=sigma_max)
+    src = ws.extra["sources"]
+    xs, ts = ws.mesh()
+    xl, tl = W.kuhn_mesh(2 * n, (-2, -2, -2), (2, 2, 2))
+    th = ws.pml["thickness"]
+    pml_l = dict(lo=(-2 + th,) * 3, hi=(2 - th,) * 3, thickness=th,
+                 sigma_max=40.0, order=ws.pml["order"])
+    gs = D.Solver(xs, ts, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", ws.dt, pml=ws.pml)
+    gl = D.Solver(xl, tl, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", ws.dt, pml=pml_l)
+    for g in (gs, gl):
+        g.set_sources(src)
+        g.autotune()
+    # element e = t n^3 + i + n j + n^2 k of the small grid <-> same type, cube + n/2
+    n3, L = n ** 3, 2 * n
+    e = np.arange(6 * n3)
+    t, c = e // n3, e % n3
+    i, j, k = c % n, (c // n) % n, c // (n * n)
+    el = t * L ** 3 + (i + n // 2) + L * (j + n // 2) + L * L * (k + n // 2)
+    cen = W.centroids(xs, ts)
+    inner = np.all(np.abs(cen) < 1 - th, axis=1)
+    steps = int(round(T / ws.dt))
+    per = max(1, steps // chunks)
+    diff = ref = 0.0
+    tt = 0.0
+    torch.cuda.synchronize()
+    start = time.perf_counter()
+    for _ in range(chunks):
+        gs.advance(per, tt)
+        gl.advance(per, tt)
+        tt += per * ws.dt
+        us = gs.state()[inner][:, 0, 0:3, :]
+        ul = gl.state()[el[inner]][:, 0, 0:3, :]
+        diff = max(diff, float(np.linalg.norm(us - ul)))
+        ref = max(ref, float(np.linalg.norm(ul)))
+    el_s = time.perf_counter() - start
+    return dict(n=n, p=p, K_small=gs.K, K_large=gl.K, steps=per * chunks, T=tt,
+                reflection=diff / ref, seconds=el_s)
+
+
 def run_cavity():
     """PEC cavity: 4^3 Kuhn grid (384 tets), p=2, vacuum, central flux, leapfrog,
     200 steps of dt = 0.3 h/(p+1)^2 from the TM110 mode; reports the L2 error of
@@ -592,6 +643,11 @@ def main():
         line["cavity"] = dict(workload="PEC cavity 4^3 (384 tets), p=2, central, leapfrog, "
                                        "TM110, 200 steps (latency regime, state fits in L2)",
                               **run_cavity())
+    if not args.no_pml and world == 1:
+        line["pml_reflection"] = dict(
+            workload="dipole in the same PML (0.25 thick, quadratic, sigma_max 40) on a 16^3 "
+                     "grid of [-1,1]^3, p=4, against [-2,2]^3 at the same h; E in the inner box",
+            **run_reflection())
     if not args.no_adjoint and world == 1:
         line["adjoint"] = dict(workload="24^3 PML mesh (82944 tets), p=3, 8 dipoles, 32 "
                                         "receivers, lognormal eps, receiver-misfit loss; FP32 "
