@@ -20,14 +20,17 @@
 //   flux_E = c_E n x dH - b_E n x (n x dE),  flux_H = c_H n x dE + b_H n x (n x dH)
 // with dX = X+ - X- the jump of the physical traces (X = A^-T x_ref per side),
 // central (c = 1/2, b = 0, Eqs. (uwc)/(cwc)) or upwind coefficients, and the
-// PEC ghost state e+ = -e-, h+ = h- on boundary faces.
+// PEC ghost state e+ = -e-, h+ = h- on boundary faces.  The kernel evaluates
+// g in the element's reference frame (face_constants_ref), where the pull-back
+// cancels the own side's A^-T and, on the three axis faces, leaves the flux
+// two components.
 //
 // Phases (separated by __syncthreads):
 //   1 load the tile's coefficients into shared memory, element geometry
 //   2 own traces (4 faces x 6 components) from shared memory, neighbour traces
 //     from global memory (the neighbour's coefficients are usually L2 hits),
 //     face constants (normal, neighbour map, flux coefficients)
-//   3 numerical flux per (face, face mode), pulled back to the element
+//   3 numerical flux per (face, face mode) in the reference frame
 //   4 right-hand side per component: volume curl + lift (+ source)
 //   5 3x3 mass-block inverse, PML terms, and the stage update
 // The reference operators are straight-line code with literal coefficients
@@ -73,10 +76,24 @@ enum FaceConst {
 constexpr int EG = 16;   // element constants per column (same slots as G_*)
 constexpr int NBS = 4;   // neighbour codes per column staged in shared memory
 
+// Face constants of the stage kernel, whose flux works in the element's
+// reference frame (see face_constants_ref), per (face, column).
+constexpr int FGR = 15;
+enum FaceConstRef {
+    FR_Q = 0,     // Q = A^T A_n^-T (9, row major): neighbour reference components -> own
+    FR_NAE = 9,   // -alpha_E: -1 on an interior face, -2 on a PEC face (e+ = -e-)
+    FR_NAH = 10,  // -alpha_H: -1 on an interior face, 0 on a PEC face (h+ = h-)
+    FR_CE = 11,   // s_T c_E
+    FR_BE = 12,   // b_E / (|det A| |A^-T m_f|)
+    FR_CH = 13,   // s_T c_H
+    FR_BH = 14    // b_H / (|det A| |A^-T m_f|)
+};
+constexpr int GM = 6;    // metric A^T A per column: entries 00, 01, 02, 11, 12, 22
+
 template <int P, typename R, int TE>
 __host__ __device__ constexpr size_t stage_smem_bytes() {
     return sizeof(R) * size_t(TE) *
-           (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FG + EG + NBS);
+           (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FGR + EG + GM + NBS);
 }
 
 // Reference operators: straight-line code with literal coefficients generated
@@ -151,6 +168,193 @@ __device__ __forceinline__ void face_constants_tab(int f, const R (&ait)[9], R d
     }
 }
 
+// Face constants of the reference-frame flux of face f (written to fc[k * TE])
+// and, when gm is not null, the element's metric A^T A (gm[k * TE]).
+//
+// With M = A^-T, the reference traces x of both sides, Q = M^-1 M_n = A^T A_n^-T
+// and the reference jump dx = Q x+ - alpha x- (alpha: 1, or the PEC ghost
+// state), the physical jump is M dx.  The identity (M a) x (M b) =
+// det M M^-T (a x b) and n = M m_f / |M m_f| give
+//   A^-1 (n x M y)         = (det M / |M m_f|) m_f x y,
+//   A^-1 (n x (n x M y))   = (det M / |M m_f|)^2 m_f x (A^T A (m_f x y)),
+// so the pulled-back fluxes g = 2|F| A^-1 flux, 2|F| = |det A| |M m_f|, are
+//   g_E =  s_T c_E m_f x dh - b_E / (|det A| |M m_f|) m_f x (A^T A (m_f x de))
+//   g_H = -s_T c_H m_f x de - b_H / (|det A| |M m_f|) m_f x (A^T A (m_f x dh))
+// with no transformation of the traces on the element's own side.  On the
+// faces x = 0, y = 0, z = 0 (m_f = -e_a) the cross products only permute
+// components, component a of g vanishes, and component a of the own trace
+// is not needed.
+template <typename R, int TE>
+__device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R det, R epsm, R mum,
+                                                   bool has_nbr, const R (&aitn)[9], R zn,
+                                                   int upwind, R* fc, R* gm) {
+    // A^T = det A adj(A^-T), row major
+    R at[9];
+    at[0] = ait[4] * ait[8] - ait[5] * ait[7];
+    at[1] = ait[2] * ait[7] - ait[1] * ait[8];
+    at[2] = ait[1] * ait[5] - ait[2] * ait[4];
+    at[3] = ait[5] * ait[6] - ait[3] * ait[8];
+    at[4] = ait[0] * ait[8] - ait[2] * ait[6];
+    at[5] = ait[2] * ait[3] - ait[0] * ait[5];
+    at[6] = ait[3] * ait[7] - ait[4] * ait[6];
+    at[7] = ait[1] * ait[6] - ait[0] * ait[7];
+    at[8] = ait[0] * ait[4] - ait[1] * ait[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) at[k] *= det;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            fc[(FR_Q + 3 * j + k) * TE] =
+                at[3 * j] * aitn[k] + at[3 * j + 1] * aitn[3 + k] + at[3 * j + 2] * aitn[6 + k];
+    const R m0 = R(f == 0 ? 1 : (f == 1 ? -1 : 0));
+    const R m1 = R(f == 0 ? 1 : (f == 2 ? -1 : 0));
+    const R m2 = R(f == 0 ? 1 : (f == 3 ? -1 : 0));
+    R vn[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) vn[r] = ait[3 * r + 0] * m0 + ait[3 * r + 1] * m1 + ait[3 * r + 2] * m2;
+    const R fs = sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
+    const R st = det < R(0) ? R(-1) : R(1);
+    const R kb = R(1) / (fabs(det) * fs);
+    const R zm = sqrt(mum / epsm);
+    const R zp = has_nbr ? zn : zm;
+    R ce = R(0.5), be = R(0), ch = R(0.5), bh = R(0);
+    if (upwind) {
+        const R ym = R(1) / zm, yp = R(1) / zp;
+        ce = zp / (zm + zp);
+        be = R(1) / (zm + zp);
+        ch = yp / (ym + yp);
+        bh = R(1) / (ym + yp);
+    }
+    fc[FR_NAE * TE] = has_nbr ? R(-1) : R(-2);
+    fc[FR_NAH * TE] = has_nbr ? R(-1) : R(0);
+    fc[FR_CE * TE] = st * ce;
+    fc[FR_BE * TE] = kb * be;
+    fc[FR_CH * TE] = st * ch;
+    fc[FR_BH * TE] = kb * bh;
+    if (gm != nullptr) {
+        gm[0 * TE] = at[0] * at[0] + at[1] * at[1] + at[2] * at[2];
+        gm[1 * TE] = at[0] * at[3] + at[1] * at[4] + at[2] * at[5];
+        gm[2 * TE] = at[0] * at[6] + at[1] * at[7] + at[2] * at[8];
+        gm[3 * TE] = at[3] * at[3] + at[4] * at[4] + at[5] * at[5];
+        gm[4 * TE] = at[3] * at[6] + at[4] * at[7] + at[5] * at[8];
+        gm[5 * TE] = at[6] * at[6] + at[7] * at[7] + at[8] * at[8];
+    }
+}
+
+// index of (i, j) in the six stored entries of a symmetric 3x3 matrix
+__host__ __device__ constexpr int sym3(int i, int j) {
+    return i > j ? sym3(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
+}
+
+// Numerical flux of modes [m0, m1) of face F (compile time) in the reference
+// frame (face_constants_ref): reads both sides' reference traces, overwrites
+// the own traces with the pulled-back fluxes g.  On an axis face only the two
+// non-zero components of g are written.  FULL: the own trace has all three
+// components and the physical jumps M dx are stored for the adjoint.
+template <int F, int NF, typename R, int TE, int MODE, typename IX>
+__device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R* trN,
+                                          const R* fg, const R* gm, const R* eg, R* jumps,
+                                          IX C, IX col, bool active) {
+    constexpr bool DO_E = (MODE != MODE_LF_H);   // E fluxes needed
+    constexpr bool DO_H = (MODE != MODE_LF_E);   // H fluxes needed
+    constexpr bool HAS_E = (MODE != MODE_LF_E);  // E jump used (H flux, upwind E flux)
+    constexpr bool HAS_H = DO_E;                 // H jump used (E flux, upwind H flux)
+    constexpr bool FULL = (MODE == MODE_RAW);
+    constexpr int A = F == 0 ? -1 : F - 1;       // axis of m_f = -e_A
+    constexpr int B = F % 3, CC = (F + 1) % 3;   // the other two axes, (A, B, CC) cyclic
+    const R* d = fg + F * FGR * TE + c;
+    R q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) q[k] = (FULL || k / 3 != A) ? d[(FR_Q + k) * TE] : R(0);
+    const R nae = d[FR_NAE * TE], nah = d[FR_NAH * TE];
+    const R cE = d[FR_CE * TE], bE = d[FR_BE * TE], cH = d[FR_CH * TE], bH = d[FR_BH * TE];
+    // A^T A, entries 00, 01, 02, 11, 12, 22 (named, so that they stay in registers)
+    const R g00 = gm[0 * TE + c], g01 = gm[1 * TE + c], g02 = gm[2 * TE + c];
+    const R g11 = gm[3 * TE + c], g12 = gm[4 * TE + c], g22 = gm[5 * TE + c];
+    R ait[9];
+    if (FULL) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
+    }
+    // entries of A^T A used on an axis face: (CC, B), (CC, CC), (B, B)
+    auto gsym = [&](int i, int j) -> R {
+        const int k = sym3(i, j);
+        return k == 0 ? g00 : k == 1 ? g01 : k == 2 ? g02 : k == 3 ? g11 : k == 4 ? g12 : g22;
+    };
+    const R gcb = gsym(CC, B), gcc = gsym(CC, CC), gbb = gsym(B, B);
+    const R kEcb = bE * gcb, kEcc = bE * gcc, kEbb = bE * gbb;
+    const R kHcb = bH * gcb, kHcc = bH * gcc, kHbb = bH * gbb;
+    // not unrolled: four copies of an unrolled loop (one per face) cost more in
+    // instruction fetch than the loop overhead they save
+#pragma unroll 1
+    for (int m = m0; m < m1; ++m) {
+        R* own = trO + (F * 6 * NF + m) * TE + c;
+        const R* nbt = trN + (F * 6 * NF + m) * TE + c;
+        R de[3] = {0, 0, 0}, dh[3] = {0, 0, 0};   // reference-frame jumps
+        if (HAS_E) {
+            R tp[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) tp[k] = nbt[k * NF * TE];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                if (FULL || r != A)
+                    de[r] = q[3 * r] * tp[0] + q[3 * r + 1] * tp[1] + q[3 * r + 2] * tp[2] +
+                            nae * own[r * NF * TE];
+        }
+        if (HAS_H) {
+            R tp[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) tp[k] = nbt[(3 + k) * NF * TE];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                if (FULL || r != A)
+                    dh[r] = q[3 * r] * tp[0] + q[3 * r + 1] * tp[1] + q[3 * r + 2] * tp[2] +
+                            nah * own[(3 + r) * NF * TE];
+        }
+        if (FULL && active) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                jumps[IX((F * 6 + r) * NF + m) * C + col] =
+                    ait[3 * r] * de[0] + ait[3 * r + 1] * de[1] + ait[3 * r + 2] * de[2];
+                jumps[IX((F * 6 + 3 + r) * NF + m) * C + col] =
+                    ait[3 * r] * dh[0] + ait[3 * r + 1] * dh[1] + ait[3 * r + 2] * dh[2];
+            }
+        }
+        if (F == 0) {
+            // m_f = (1, 1, 1): m x y = (y2 - y1, y0 - y2, y1 - y0)
+            const R we[3] = {de[2] - de[1], de[0] - de[2], de[1] - de[0]};
+            const R wh[3] = {dh[2] - dh[1], dh[0] - dh[2], dh[1] - dh[0]};
+            if (DO_E) {   // z = b_E A^T A w_e
+                const R z0 = bE * (g00 * we[0] + g01 * we[1] + g02 * we[2]);
+                const R z1 = bE * (g01 * we[0] + g11 * we[1] + g12 * we[2]);
+                const R z2 = bE * (g02 * we[0] + g12 * we[1] + g22 * we[2]);
+                own[0 * NF * TE] = cE * wh[0] - (z2 - z1);
+                own[1 * NF * TE] = cE * wh[1] - (z0 - z2);
+                own[2 * NF * TE] = cE * wh[2] - (z1 - z0);
+            }
+            if (DO_H) {   // z = b_H A^T A w_h
+                const R z0 = bH * (g00 * wh[0] + g01 * wh[1] + g02 * wh[2]);
+                const R z1 = bH * (g01 * wh[0] + g11 * wh[1] + g12 * wh[2]);
+                const R z2 = bH * (g02 * wh[0] + g12 * wh[1] + g22 * wh[2]);
+                own[3 * NF * TE] = -cH * we[0] - (z2 - z1);
+                own[4 * NF * TE] = -cH * we[1] - (z0 - z2);
+                own[5 * NF * TE] = -cH * we[2] - (z1 - z0);
+            }
+        } else {
+            // m_f = -e_A: (m x y)_A = 0, (m x y)_B = y_CC, (m x y)_CC = -y_B
+            if (DO_E) {
+                own[B * NF * TE] = cE * dh[CC] - kEcb * de[CC] + kEcc * de[B];
+                own[CC * NF * TE] = -cE * dh[B] + kEbb * de[CC] - kEcb * de[B];
+            }
+            if (DO_H) {
+                own[(3 + B) * NF * TE] = -cH * de[CC] - kHcb * dh[CC] + kHcc * dh[B];
+                own[(3 + CC) * NF * TE] = cH * de[B] + kHbb * dh[CC] - kHcb * dh[B];
+            }
+        }
+    }
+}
+
 // Right-hand side rows [LO, HI) of component `comp` (before the mass inverse):
 // volume curl of the other field plus the lift of the pulled-back fluxes.
 template <int P, typename R, int TE, int LO, int HI>
@@ -165,7 +369,10 @@ __device__ __forceinline__ void rhs_rows(int comp, int c, const R* us, const R* 
     const int j = comp % 3;
     const int srcf = comp < 3 ? 3 : 0;
     const R sg = comp < 3 ? sgn : -sgn;
+    // The pulled-back flux of face a + 1 (normal -e_a) has no component a, so
+    // component j lifts the fluxes of the three other faces only.
     const R* base = us + c;
+    const R* g = trO + comp * NF * TE + c;    // face f of this component: g + f * 6 * NF * TE
     switch (j) {
         case 0:
             DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 2) * N * TE, TE, sg, acc);
@@ -180,10 +387,12 @@ __device__ __forceinline__ void rhs_rows(int comp, int c, const R* us, const R* 
             DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 0) * N * TE, TE, -sg, acc);
             break;
     }
-    LiftOp<P, 0>::template apply<R, LO, HI>(trO + ((0 * 6 + comp) * NF) * TE + c, TE, acc);
-    LiftOp<P, 1>::template apply<R, LO, HI>(trO + ((1 * 6 + comp) * NF) * TE + c, TE, acc);
-    LiftOp<P, 2>::template apply<R, LO, HI>(trO + ((2 * 6 + comp) * NF) * TE + c, TE, acc);
-    LiftOp<P, 3>::template apply<R, LO, HI>(trO + ((3 * 6 + comp) * NF) * TE + c, TE, acc);
+    // one copy of each lift, skipped by a branch that is uniform over the
+    // group (lifts inside the cases above would triple the code of this phase)
+    LiftOp<P, 0>::template apply<R, LO, HI>(g + 0 * 6 * NF * TE, TE, acc);
+    if (j != 0) LiftOp<P, 1>::template apply<R, LO, HI>(g + 1 * 6 * NF * TE, TE, acc);
+    if (j != 1) LiftOp<P, 2>::template apply<R, LO, HI>(g + 2 * 6 * NF * TE, TE, acc);
+    if (j != 2) LiftOp<P, 3>::template apply<R, LO, HI>(g + 3 * 6 * NF * TE, TE, acc);
 }
 
 template <int P, typename R, int TE, int NPART>
@@ -217,9 +426,10 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     R* us = reinterpret_cast<R*>(smem_raw);      // [6N][TE]
     R* trO = us + 6 * N * TE;                    // [4][6][NF][TE]  own traces -> g
     R* trN = trO + 24 * NF * TE;                 // [4][6][NF][TE]  nbr traces -> rhs [6][N][TE]
-    R* fg = trN + 24 * NF * TE;                  // [4][FG][TE]
-    R* eg = fg + 4 * FG * TE;                    // [EG][TE]
-    int32_t* nbs = reinterpret_cast<int32_t*>(eg + EG * TE);   // [4][TE] neighbour codes
+    R* fg = trN + 24 * NF * TE;                  // [4][FGR][TE]
+    R* eg = fg + 4 * FGR * TE;                   // [EG][TE]
+    R* gm = eg + EG * TE;                        // [GM][TE] metric A^T A
+    int32_t* nbs = reinterpret_cast<int32_t*>(gm + GM * TE);   // [4][TE] neighbour codes
 
     const int c = threadIdx.x % TE;
     const int grp = threadIdx.x / TE;
@@ -269,8 +479,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         const R epsm = active ? gr[IX(G_EPS) * K + e] : R(1);
         const R mum = active ? gr[IX(G_MU) * K + e] : R(1);
         const R zn = active ? fn[IX(FNB_Z) * K] : R(1);
-        face_constants_tab<R, TE>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
-                                  prm.upwind, fg + f * FG * TE + c);
+        face_constants_ref<R, TE>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
+                                  prm.upwind, fg + f * FGR * TE + c, f == 0 ? gm + c : nullptr);
     };
     // neighbour code of this group's round-0 item, loaded with the other
     // independent loads so that the dependent gather starts one round trip in
@@ -367,6 +577,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int f = 2 * fp + h;
+                    // the flux on face a + 1 (normal -e_a) does not use component a
+                    // of the own trace, except for the adjoint's physical jumps
+                    if (MODE != MODE_RAW && f == ocomp % 3 + 1) continue;
                     trace_any<P, R>(f, v, acc);
                     R* dst = trO + ((f * 6 + ocomp) * NF) * TE + c;
 #pragma unroll
@@ -380,88 +593,20 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     __syncthreads();
 
     // ---- phase 3: numerical flux per (face, chunk of face modes) -------------
+    // in the element's reference frame, one code path per face (the face of an
+    // item is uniform over its warp-sized group)
     {
         constexpr int CHUNKS = NG >= 12 ? (NG / 4) : 1;      // face-mode chunks per face
+        R* jp = static_cast<R*>(prm.jumps);
         for (int it = grp; it < 4 * CHUNKS; it += NG) {
             const int f = it / CHUNKS;
             const int ch = it % CHUNKS;
-            const R* d = fg + f * FG * TE + c;
-            R ait[9], aitn[9], n[3];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                ait[k] = eg[(G_AIT + k) * TE + c];
-                aitn[k] = d[(FC_AITN + k) * TE];
-            }
-#pragma unroll
-            for (int r = 0; r < 3; ++r) n[r] = d[(FC_N + r) * TE];
-            const bool bnd = d[FC_BND * TE] != R(0);
-            const R twoF = d[FC_TWOF * TE];
-            const R ce = d[FC_CE * TE], be = d[FC_BE * TE];
-            const R chc = d[FC_CH * TE], bh = d[FC_BH * TE];
             const int m0 = ch * NF / CHUNKS, m1 = (ch + 1) * NF / CHUNKS;
-            for (int m = m0; m < m1; ++m) {
-                R* own = trO + (f * 6 * NF + m) * TE + c;
-                const R* nbt = trN + (f * 6 * NF + m) * TE + c;
-                R dE[3] = {0, 0, 0}, dH[3] = {0, 0, 0};
-                // physical traces X = A^-T x_ref on each side
-                if (MODE != MODE_LF_E) {   // E traces: flux_H and the upwind part of flux_E
-                    R tm[3], tp[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        tm[k] = own[k * NF * TE];
-                        tp[k] = nbt[k * NF * TE];
-                    }
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        const R em = ait[3 * r] * tm[0] + ait[3 * r + 1] * tm[1] + ait[3 * r + 2] * tm[2];
-                        const R ep = aitn[3 * r] * tp[0] + aitn[3 * r + 1] * tp[1] + aitn[3 * r + 2] * tp[2];
-                        dE[r] = bnd ? R(-2) * em : ep - em;
-                    }
-                }
-                if (DO_E) {
-                    R tm[3], tp[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        tm[k] = own[(3 + k) * NF * TE];
-                        tp[k] = nbt[(3 + k) * NF * TE];
-                    }
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        const R hm = ait[3 * r] * tm[0] + ait[3 * r + 1] * tm[1] + ait[3 * r + 2] * tm[2];
-                        const R hp = aitn[3 * r] * tp[0] + aitn[3 * r + 1] * tp[1] + aitn[3 * r + 2] * tp[2];
-                        dH[r] = bnd ? R(0) : hp - hm;
-                    }
-                }
-                if (MODE == MODE_RAW && active) {
-                    R* jp = static_cast<R*>(prm.jumps);
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        jp[IX((f * 6 + r) * NF + m) * C + col] = dE[r];
-                        jp[IX((f * 6 + 3 + r) * NF + m) * C + col] = dH[r];
-                    }
-                }
-                R nxdE[3], nxdH[3], nnxdE[3], nnxdH[3];
-                cross3(n, dE, nxdE);
-                cross3(n, dH, nxdH);
-                cross3(n, nxdE, nnxdE);
-                cross3(n, nxdH, nnxdH);
-                if (DO_E) {
-                    R fl[3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) fl[r] = ce * nxdH[r] - be * nnxdE[r];
-                    // g = 2|F| A^-1 flux, A^-1 = (A^-T)^T
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-                        own[j * NF * TE] = twoF * (ait[j] * fl[0] + ait[3 + j] * fl[1] + ait[6 + j] * fl[2]);
-                }
-                if (DO_H) {
-                    R fl[3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) fl[r] = chc * nxdE[r] + bh * nnxdH[r];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-                        own[(3 + j) * NF * TE] = -twoF * (ait[j] * fl[0] + ait[3 + j] * fl[1] + ait[6 + j] * fl[2]);
-                }
+            switch (f) {
+                case 0: flux_face<0, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
+                case 1: flux_face<1, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
+                case 2: flux_face<2, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
+                default: flux_face<3, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
             }
         }
     }
@@ -533,34 +678,17 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         if (!DO_H && field == 1) continue;
         if (!active) continue;
         const int fb = 3 * field;   // first component of this field
-        R ait[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
         const R det = eg[G_DET * TE + c];
         const R mat = field == 0 ? eg[G_EPS * TE + c] : eg[G_MU * TE + c];
-        // A^T = adj(A^-T) det A
-        R AT[3][3];
-        AT[0][0] = ait[4] * ait[8] - ait[5] * ait[7];
-        AT[0][1] = ait[2] * ait[7] - ait[1] * ait[8];
-        AT[0][2] = ait[1] * ait[5] - ait[2] * ait[4];
-        AT[1][0] = ait[5] * ait[6] - ait[3] * ait[8];
-        AT[1][1] = ait[0] * ait[8] - ait[2] * ait[6];
-        AT[1][2] = ait[2] * ait[3] - ait[0] * ait[5];
-        AT[2][0] = ait[3] * ait[7] - ait[4] * ait[6];
-        AT[2][1] = ait[1] * ait[6] - ait[0] * ait[7];
-        AT[2][2] = ait[0] * ait[4] - ait[1] * ait[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) AT[a][b] *= det;
-        // the 3x3 mass-block inverse A^T A / (mat |det|), symmetric
+        // the 3x3 mass-block inverse A^T A / (mat |det|), symmetric, from the
+        // metric that phase 1 stored
         R B[3][3];
         const R inv = R(1) / (mat * fabs(det));
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int k = j; k < 3; ++k) {
-                B[j][k] = inv * (AT[j][0] * AT[k][0] + AT[j][1] * AT[k][1] + AT[j][2] * AT[k][2]);
+                B[j][k] = inv * gm[sym3(j, k) * TE + c];
                 B[k][j] = B[j][k];
             }
         // PML: (A^T D A^-T)[j][k] = sum_a A^T[j][a] D_a A^-T[a][k] for D = eta, Sigma, xi
@@ -568,6 +696,24 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         if (prm.pml != nullptr) pi = prm.pml[e];
         R ETA[3][3], SIG[3][3], XI[3][3];
         if (pi >= 0) {
+            R ait[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
+            // A^T = adj(A^-T) det A
+            R AT[3][3];
+            AT[0][0] = ait[4] * ait[8] - ait[5] * ait[7];
+            AT[0][1] = ait[2] * ait[7] - ait[1] * ait[8];
+            AT[0][2] = ait[1] * ait[5] - ait[2] * ait[4];
+            AT[1][0] = ait[5] * ait[6] - ait[3] * ait[8];
+            AT[1][1] = ait[0] * ait[8] - ait[2] * ait[6];
+            AT[1][2] = ait[2] * ait[3] - ait[0] * ait[5];
+            AT[2][0] = ait[3] * ait[7] - ait[4] * ait[6];
+            AT[2][1] = ait[1] * ait[6] - ait[0] * ait[7];
+            AT[2][2] = ait[0] * ait[4] - ait[1] * ait[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) AT[a][b] *= det;
             const R sx = eg[(G_SIG + 0) * TE + c], sy = eg[(G_SIG + 1) * TE + c],
                     sz = eg[(G_SIG + 2) * TE + c];
             const R sg3[3] = {sx, sy, sz};
