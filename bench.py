@@ -600,13 +600,13 @@ def main():
     if os.path.exists(tfile):
         import re
         txt = open(tfile).read()
-        m = re.search(r"traffic_bytes_per_element_stage:\s*(\d+)", txt)
-        mv = re.search(r"profiled_variant:\s*(\d+)", txt)
-        mg = re.search(r"profiled_tile_groups:\s*(\d+)", txt)
         groups = (r32["tuned"] or {}).get("tile_groups", 1)
-        # counters of another kernel variant or tile order say nothing about this one
-        if m and mv and mg and int(mv.group(1)) == chosen and int(mg.group(1)) == groups:
-            traffic = int(m.group(1)) * r32["K"] * r32["S"]
+        # one line per profiled (tile shape, tile order); counters of another
+        # shape or order say nothing about this one
+        for m in re.finditer(r"traffic_bytes_per_element_stage variant=(\d+) tile_groups=(\d+):"
+                             r"\s*(\d+)", txt):
+            if int(m.group(1)) == chosen and int(m.group(2)) == groups:
+                traffic = int(m.group(3)) * r32["K"] * r32["S"]
     line = {
         "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps,

@@ -205,11 +205,15 @@ int dgm_adjoint(dgm_plan* plan, int64_t n_steps, double t0, const double* drecor
 /* Autotuner: times each compiled tile shape (columns per CTA x threads per
  * CTA) of the LSRK4 stage kernel on the plan's current state, `reps` launches
  * each, and keeps the fastest for later dgm_advance / dgm_batch_create calls;
- * then times the tile visiting orders of dgm_set_tile_groups for that shape.
- * The plan's state is not modified: outputs go to `workspace`, device memory
- * of 2*align256(bytes_fields) + 2*align256(bytes_aux) bytes.  ms_out (host,
- * may be NULL) receives the mean time per launch of each variant.
- * Synchronises the bound stream. */
+ * then times the tile visiting orders of dgm_set_tile_groups for that shape
+ * (at least ten launches each).  The plan's state is only read.  An LSRK4
+ * plan is timed on stage sequences as dgm_advance runs them: the first launch
+ * reads the state and writes `workspace`, later ones alternate between
+ * `workspace` and the plan's second field (and auxiliary) buffer, which hold
+ * nothing between steps; other plans write `workspace` only.  workspace:
+ * device memory of 2*align256(bytes_fields) + 2*align256(bytes_aux) bytes,
+ * 256-byte aligned.  ms_out (host, may be NULL) receives the mean time per
+ * launch of each variant.  Synchronises the bound stream. */
 int dgm_autotune(dgm_plan* plan, void* workspace, int32_t reps, float* ms_out);
 int dgm_autotune_info(const dgm_plan* plan, int32_t* n_variants, int32_t* chosen);
 /* Select a tile-shape variant explicitly (0 .. n_variants-1). */
@@ -226,8 +230,9 @@ int dgm_set_index64(dgm_plan* plan, int32_t force);
  * take tiles from G equal segments of the columns in turn, which keeps the
  * neighbours' coefficients of meshes numbered in G blocks (e.g. a Kuhn grid
  * numbered by tetrahedron type) in L2; 1 = plain order.  Results do not
- * depend on it.  dgm_autotune picks it after the tile shape (candidates 1,
- * 2, 3, 4, 6, 8, 12); DGM_EINVAL outside 1..64. */
+ * depend on it.  dgm_autotune picks it after the tile shape: the fastest of
+ * 1, 2, 3, 4, 6, 8, 12, or 1 unless that is at least 1 % faster than the plain
+ * order; DGM_EINVAL outside 1..64. */
 int dgm_set_tile_groups(dgm_plan* plan, int32_t groups);
 int dgm_get_tile_groups(const dgm_plan* plan, int32_t* groups);
 

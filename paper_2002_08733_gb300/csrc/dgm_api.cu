@@ -1208,23 +1208,49 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
     const size_t fb = align256(info.bytes_fields), ab = align256(info.bytes_aux);
     StageParams prm;
     stage_params(P, prm);
-    prm.u = P->fields[P->cur];
-    prm.aux = P->aux[P->cur];
-    prm.u_out = ws;
+    // An LSRK4 plan is timed on stage sequences as the time loop runs them:
+    // the first (untimed) launch reads the state and writes workspace buffer
+    // 0, later launches ping-pong between that buffer and the plan's second
+    // field buffer with the stage coefficients in turn, so each launch reads
+    // an input that the previous one wrote, as in a step, and the tile
+    // order's effect on L2 reuse is measured as a step sees it.  Between
+    // steps the second field buffer (and the second auxiliary buffer) hold
+    // nothing, so the state is only read.  Other plans repeat one launch from
+    // the state into the workspace.
+    const bool seq = P->opt.integrator == DGM_LSRK4 && P->fields[1 - P->cur] != nullptr &&
+                     (!ab || P->aux[1 - P->cur] != nullptr);
+    void* fbuf[2] = {ws, seq ? P->fields[1 - P->cur] : nullptr};
+    void* abuf[2] = {ab ? ws + 2 * fb : nullptr, seq && ab ? P->aux[1 - P->cur] : nullptr};
     prm.res = ws + fb;
-    prm.aux_out = ab ? ws + 2 * fb : nullptr;
     prm.aux_res = ab ? ws + 2 * fb + ab : nullptr;
-    prm.a = 0.0;
-    prm.b = LSRK_B[0];
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    // mean time of `n` launches of the current prm (after one warm launch)
+    // mean time of `n` launches of the current shape and order (after one warm launch)
     auto time_it = [&](int n, float* ms) -> int {
+        prm.u = P->fields[P->cur];
+        prm.aux = P->aux[P->cur];
+        prm.u_out = fbuf[0];
+        prm.aux_out = abuf[0];
+        prm.a = 0.0;
+        prm.b = LSRK_B[0];
         int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
         if (rc) return fail(rc, "stage kernel launch failed");
+        int src = 0;   // buffer holding the last output
         cudaEventRecord(e0, P->stream);
-        for (int r = 0; r < n; ++r) P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+        for (int r = 0; r < n; ++r) {
+            if (seq) {
+                const int k = (r + 1) % 5;
+                prm.u = fbuf[src];
+                prm.aux = abuf[src];
+                prm.u_out = fbuf[1 - src];
+                prm.aux_out = abuf[1 - src];
+                prm.a = LSRK_A[k];
+                prm.b = LSRK_B[k];
+                src = 1 - src;
+            }
+            P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+        }
         cudaEventRecord(e1, P->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
@@ -1254,15 +1280,14 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
         float g_ms[7] = {0};
         for (int i = 0; i < 7 && rc == DGM_OK; ++i) {
             prm.tile_groups = cand[i];
-            rc = time_it(reps < 5 ? 5 : reps, &g_ms[i]);
+            rc = time_it(reps < 10 ? 10 : reps, &g_ms[i]);   // two steps' stages at least
         }
         if (rc == DGM_OK) {
-            float bms = g_ms[0];
+            // the fastest order, unless it is not a clear gain over the plain order
+            int bi = 0;
             for (int i = 1; i < 7; ++i)
-                if (g_ms[i] < 0.99f * bms) {   // only a clear gain moves off the plain order
-                    bms = g_ms[i];
-                    best_g = cand[i];
-                }
+                if (g_ms[i] < g_ms[bi]) bi = i;
+            if (g_ms[bi] < 0.99f * g_ms[0]) best_g = cand[bi];
         }
     }
     cudaEventDestroy(e0);

@@ -100,6 +100,37 @@ def test_autotuned_variants_match_oracle(D):
         assert rel_l2(g2.state(), ref) < 1e-5, v
 
 
+def test_autotune_reads_state_only(D):
+    """The autotuner times LSRK4 stage sequences in its workspace and the
+    plan's second field and auxiliary buffers: the state (fields and PML
+    auxiliaries, mid-run) is left bit for bit, and the steps after it equal
+    those of an untuned twin plan set to the same shape and tile order."""
+    xyz, tets = W.kuhn_mesh(2, (-1, -1, -1), (1, 1, 1), jitter=0.1, seed=73)
+    pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
+    srcs = [W.dipole((0.1, 0.05, -0.02), 2.0, 1.0)]
+    p = 3
+    dt = W.stable_dt(1.0, p)
+    u = W.random_state(len(tets), 1, p, seed=75) * 1e-2
+    twins = []
+    for _ in range(2):
+        g = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", dt, S=1, pml=pml)
+        g.set_sources(srcs)
+        g.set_state(u)
+        g.advance(2, 0.0)
+        twins.append(g)
+    a, b = twins
+    aux = lambda g: g.from_device(g.aux[g.current()])
+    st0, aux0 = a.state().copy(), aux(a).copy()
+    assert np.abs(aux0).max() > 0
+    chosen, ms = a.autotune()
+    assert np.array_equal(a.state(), st0) and np.array_equal(aux(a), aux0)
+    b.set_variant(chosen)
+    b.set_tile_groups(a.tile_groups())
+    for g in (a, b):
+        g.advance(2, 2 * dt)
+    assert np.array_equal(a.state(), b.state()) and np.array_equal(aux(a), aux(b))
+
+
 _HIGH_P_REF = {}
 
 
