@@ -506,11 +506,25 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
         const R dt = R(prm.dt);
         R gmass = R(0), gpml = R(0);   // partial sums in the kernel's precision
         const int lo = part * N / NPART, hi = (part + 1) * N / NPART;
-        for (int l = lo; l < hi; ++l) {
+        // the item's forward right-hand-side and adjoint rows, all requested
+        // before the arithmetic so that their round trips overlap
+        constexpr int RP = (N + NPART - 1) / NPART;
+        R rawv[RP], luv[RP];
+#pragma unroll
+        for (int i = 0; i < RP; ++i) {
+            const bool ok = lo + i < hi;
+            const IX gi = IX(comp * N + lo + i) * C + col;
+            rawv[i] = ok ? raw[gi] : R(0);
+            luv[i] = ok ? lu[gi] : R(0);
+        }
+#pragma unroll
+        for (int i = 0; i < RP; ++i) {
+            const int l = lo + i;
+            if (l >= hi) break;
             R w = rh[(comp * N + l) * TE + c];
             const IX gi = IX(comp * N + l) * C + col;
             // mass term of the gradient: -(1/mat) rho_c . rhs_c
-            gmass += rs[(comp * N + l) * TE + c] * raw[gi];
+            gmass += rs[(comp * N + l) * TE + c] * rawv[i];
             if (pi >= 0) {
                 const R l0 = us[((fb + 0) * N + l) * TE + c];
                 const R l1 = us[((fb + 1) * N + l) * TE + c];
@@ -531,7 +545,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 && P <= 3 ? 2 : 1) adjoint_
                 const R u2 = uf[IX((fb + 2) * N + l) * C + col];
                 gpml += lj * apj / (mat * mat) + pj * (xiR[0] * u0 + xiR[1] * u1 + xiR[2] * u2);
             }
-            lu[gi] += dt * w;
+            lu[gi] = luv[i] + dt * w;
         }
         const int slot = comp < 3 ? 0 : 1;
         gp[(slot * 6 * NPART + it) * TE + c] = double(-gmass / mat + gpml);
