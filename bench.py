@@ -447,6 +447,26 @@ def run_adjoint(steps, n=24):
                 grad_eps_norm=float(eps.grad.norm()), grad_mu_norm=float(mu_p.grad.norm()))
 
 
+TRAFFIC_PROFILE = "stage_kernel_full_jittered_sphere_n28_p3_fp32.md"
+
+
+def profiled_traffic(path, variant, groups, columns):
+    """DRAM bytes of one stage launch from the committed ncu summary: its line
+    `traffic_bytes_per_element_stage variant=V tile_groups=G: B` for the tile
+    shape and tile order this run uses, times the columns; None when the
+    summary has no line for them (counters of another shape or order say
+    nothing about this one)."""
+    import re
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    for m in re.finditer(r"traffic_bytes_per_element_stage variant=(\d+) tile_groups=(\d+):"
+                         r"\s*(\d+)", txt):
+        if int(m.group(1)) == variant and int(m.group(2)) == groups:
+            return int(m.group(3)) * columns
+    return None
+
+
 def run_e2e(g, steps, t0, world=1):
     """End-to-end: per step, pinned host state -> device, one step, device -> host,
     through the C-ABI call with host buffers; whole-job rate over the ranks."""
@@ -594,19 +614,10 @@ def main():
     achieved = bytes_step / 5 / (launch_ms * 1e-3) / 1e9
     # DRAM traffic of one stage launch from the committed ncu summary of the same
     # kernel (small case, scaled by the element count; see the summary file)
-    traffic = None
     chosen = (r32["tuned"] or {}).get("variant", 0)
-    tfile = os.path.join(ROOT, "profiles", "stage_kernel_full_jittered_sphere_n28_p3_fp32.md")
-    if os.path.exists(tfile):
-        import re
-        txt = open(tfile).read()
-        groups = (r32["tuned"] or {}).get("tile_groups", 1)
-        # one line per profiled (tile shape, tile order); counters of another
-        # shape or order say nothing about this one
-        for m in re.finditer(r"traffic_bytes_per_element_stage variant=(\d+) tile_groups=(\d+):"
-                             r"\s*(\d+)", txt):
-            if int(m.group(1)) == chosen and int(m.group(2)) == groups:
-                traffic = int(m.group(3)) * r32["K"] * r32["S"]
+    groups = (r32["tuned"] or {}).get("tile_groups", 1)
+    traffic = profiled_traffic(os.path.join(ROOT, "profiles", TRAFFIC_PROFILE), chosen, groups,
+                               r32["K"] * r32["S"])
     line = {
         "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps,
