@@ -612,8 +612,8 @@ def main():
     launch_ms = r32["ms"] / r32["launches"]
     bytes_step = stage_bytes(r32["K"], r32["N"], r32["S"], r32["real_size"])
     achieved = bytes_step / 5 / (launch_ms * 1e-3) / 1e9
-    # DRAM traffic of one stage launch from the committed ncu summary of the same
-    # kernel (small case, scaled by the element count; see the summary file)
+    # DRAM traffic of one stage launch: the committed ncu summary's full-size
+    # figure for this tile shape and tile order, per element-stage times columns
     chosen = (r32["tuned"] or {}).get("variant", 0)
     groups = (r32["tuned"] or {}).get("tile_groups", 1)
     traffic = profiled_traffic(os.path.join(ROOT, "profiles", TRAFFIC_PROFILE), chosen, groups,
