@@ -129,9 +129,10 @@ __device__ __forceinline__ double source_time(double t, double f0, double bw, do
     return sin(twopi * f0 * tau) * exp(-tau * tau / (2.0 * s * s));
 }
 
-// Face constants of face f of one element (written to fc[k * TE]): unit outward
-// normal, the neighbour's A^-T (own on a PEC face), flux coefficients, 2|F|,
-// PEC flag.  2|F| n = |det A| A^-T m_f with m_f = 2|F_hat| n_hat of the
+// Face constants of face f of one element for the physical-frame flux (the
+// adjoint kernel's; the stage kernel uses face_constants_ref), written to
+// fc[k * TE]: unit outward normal, the neighbour's A^-T (own on a PEC face),
+// flux coefficients, 2|F|, PEC flag.  2|F| n = |det A| A^-T m_f with m_f = 2|F_hat| n_hat of the
 // reference face: (1,1,1), (-1,0,0), (0,-1,0), (0,0,-1).  The neighbour's A^-T
 // and impedance come from the per-face neighbour table (own values on a
 // boundary face), so every input is one coalesced load.
