@@ -18,9 +18,10 @@ from __future__ import annotations
 
 import os
 
-os.environ.setdefault("OMP_NUM_THREADS", "1")
+# the oracle's per-element dense products stay single-threaded; its sparse
+# operator product runs on PyTorch's CPU threads, one per host core (reported
+# as cores)
 os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-os.environ.setdefault("MKL_NUM_THREADS", "1")
 
 import argparse
 import json
@@ -490,29 +491,115 @@ def run_e2e(g, steps, t0, world=1):
                 h2d_bytes_per_step=int(nbytes), d2h_bytes_per_step=int(nbytes))
 
 
-def cpu_reference(seconds_budget=20.0, n=4):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: the same
-    jittered-sphere problem (p, flux, LSRK4, materials, jitter) on an n^3 grid."""
-    from oracle.assemble import Assembly
+SPHERE_REPLICA_N = 3
+DIPOLE_REPLICA = dict(n=2, src=(0.13, -0.21, 0.08),
+                      pml=dict(lo=(-0.75,) * 3, hi=(0.75,) * 3, thickness=0.25,
+                               sigma_max=40.0, order=2))
+
+
+def host_threads():
+    """One PyTorch CPU thread per core this process may run on."""
+    import torch
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    torch.set_num_threads(max(1, int(n or 1)))
+    return torch.get_num_threads()
+
+
+def cpu_reference():
+    """The FP64 oracle, as it stands, on bounded samples of the two benchmarked
+    workloads, at their full step counts and time steps, on replica meshes:
+
+    * jittered sphere (p = 3, eps = 4 sphere, upwind, LSRK4, Gaussian pulse) on
+      a 3^3 jittered grid (162 elements), 1000 steps -- timed: the CPU baseline;
+    * dipole in the PML (p = 4, PML 0.25 thick, sigma_max 40, z dipole from rest)
+      on a 2^3 grid of [-1,1]^3 (48 elements), 2000 steps.
+
+    Returns the baseline record and, for each replica, what the GPU runs need
+    to be compared with the oracle (initial state from the oracle's own
+    projection, final oracle state)."""
+    import torch
+    from oracle.assemble import Assembly, pml_sigma
     from oracle.mesh import Mesh
     from oracle.solver import Solver as OSolver
-    w = W.jittered_sphere(n=n)
+    host_threads()
+    full = W.jittered_sphere()
+    w = W.jittered_sphere(n=SPHERE_REPLICA_N)
     xyz, tets, eps = build_problem(w)
     o = OSolver(Assembly(Mesh(xyz, tets), w.p, eps, 1.0, w.flux))
-    x = np.zeros((o.asm.ndof, 1))
-    x[:] = 1e-3
-    steps, start = 0, time.perf_counter()
-    while True:
-        x = o.lsrk4(x, 0.0, w.dt, 1)
-        steps += 1
-        el = time.perf_counter() - start
-        if el > seconds_budget or steps >= 1000:
-            break
+    r0 = np.asarray(full.extra["r0"])
+    ey = o.project(lambda q: np.stack([0 * q[:, 0], np.exp(-((q - r0) ** 2).sum(1) / 0.01),
+                                       0 * q[:, 0]], axis=1), "E")
+    u0 = np.zeros((len(tets), 1, 6, w.N))
+    u0[:, 0, 0:3] = ey
+    start = time.perf_counter()
+    x = o.lsrk4(o.pack(u0), 0.0, full.dt, full.steps)
+    el = time.perf_counter() - start
     dofs = 6 * o.asm.N * o.asm.K
-    return dict(value=dofs * steps / el, unit=UNIT, cores=1, kind="oracle",
-                sample="jittered-sphere workload on a %d^3 Kuhn grid (%d elements, p=%d), "
-                       "%d LSRK4 steps, assembly excluded" % (n, o.asm.K, w.p, steps)), \
-        (o, w, dofs)
+    base = dict(value=dofs * full.steps / el, unit=UNIT, cores=torch.get_num_threads(),
+                kind="oracle", seconds=el,
+                sample="jittered-sphere workload (p=3, upwind, LSRK4, eps=4 sphere, Gaussian "
+                       "pulse) on a %d^3 jittered Kuhn grid (%d elements), %d LSRK4 steps of "
+                       "dt=%.4g as in the full workload; assembly and projection excluded; "
+                       "the sparse operator product on %d PyTorch CPU threads"
+                       % (SPHERE_REPLICA_N, o.asm.K, full.steps, full.dt,
+                          torch.get_num_threads()))
+    sphere = dict(xyz=xyz, tets=tets, eps=eps, p=w.p, dt=full.dt, steps=full.steps, u0=u0,
+                  ref=o.unpack(x)[0],
+                  workload="jittered sphere on a %d^3 replica grid (%d elements), p=3, %d "
+                           "steps of dt=%.4g" % (SPHERE_REPLICA_N, o.asm.K, full.steps, full.dt))
+    fd = W.dipole_pml()
+    r = DIPOLE_REPLICA
+    xyz, tets = W.kuhn_mesh(r["n"], (-1, -1, -1), (1, 1, 1))
+    m = Mesh(xyz, tets)
+    pm = r["pml"]
+    sig = pml_sigma(m.centroids(), pm["lo"], pm["hi"], pm["thickness"], pm["sigma_max"],
+                    pm["order"])
+    src = [W.dipole(r["src"], 2.0, 1.0)]
+    od = OSolver(Assembly(m, fd.p, 1.0, 1.0, "upwind", sigma=sig), S=1, sources=src)
+    xd = od.lsrk4(np.zeros((od.asm.ndof, 1)), 0.0, fd.dt, fd.steps)
+    ud, ad = od.unpack(xd)
+    dipole = dict(xyz=xyz, tets=tets, p=fd.p, dt=fd.dt, steps=fd.steps, src=src, pml=pm,
+                  ref=ud, ref_aux=ad,
+                  workload="dipole in the PML on a %d^3 replica grid of [-1,1]^3 (%d elements, "
+                           "%d in the layer), p=4, %d steps of dt=%.4g from rest"
+                           % (r["n"], od.asm.K, int(np.any(sig > 0, axis=1).sum()), fd.steps,
+                              fd.dt))
+    return base, sphere, dipole
+
+
+def _errors(got, ref):
+    return dict(rel_l2=float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                rel_max=float(np.abs(got - ref).max() / np.abs(ref).max()))
+
+
+def replica_accuracy(sphere, dipole):
+    """FP32 (autotuned) and FP64 GPU runs of the two replicas against the oracle
+    at the full step counts: relative L2 and element-wise error of the final
+    state (fields; PML auxiliaries for the dipole)."""
+    from paper_2002_08733_gb300 import dgmax as D
+    out = {"jittered_sphere": {"workload": sphere["workload"]},
+           "dipole_pml": {"workload": dipole["workload"]}}
+    for prec in ("fp32", "fp64"):
+        c = sphere
+        g = D.Solver(c["xyz"], c["tets"], c["eps"], 1.0, c["p"], prec, "upwind", "lsrk4",
+                     c["dt"])
+        if prec == "fp32":
+            g.autotune()
+        g.set_state(c["u0"])
+        g.advance(c["steps"], 0.0)
+        out["jittered_sphere"][prec] = _errors(g.state(), c["ref"])
+        c = dipole
+        g = D.Solver(c["xyz"], c["tets"], 1.0, 1.0, c["p"], prec, "upwind", "lsrk4", c["dt"],
+                     pml=c["pml"])
+        g.set_sources(c["src"])
+        if prec == "fp32":
+            g.autotune()
+        g.advance(c["steps"], 0.0)
+        e = _errors(g.state(), c["ref"])
+        ea = _errors(g.from_device(g.aux[g.current()]), c["ref_aux"][g.pml_elements()])
+        e.update(aux_rel_l2=ea["rel_l2"], aux_rel_max=ea["rel_max"])
+        out["dipole_pml"][prec] = e
+    return out
 
 
 def main():
@@ -554,30 +641,41 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        import torch
+        host_threads()
         steps, warm = args.steps, args.warmup
         from oracle.assemble import Assembly
         from oracle.mesh import Mesh
         from oracle.solver import Solver as OSolver
-        ws = W.jittered_sphere(n=4)
+        n_ref = 4
+        ws = W.jittered_sphere(n=n_ref)
         xyz, tets, eps = build_problem(ws)
         o = OSolver(Assembly(Mesh(xyz, tets), ws.p, eps, 1.0, ws.flux))
         x = np.full((o.asm.ndof, 1), 1e-3)
         for _ in range(warm):
-            x = o.lsrk4(x, 0.0, ws.dt, 1)
+            x = o.lsrk4(x, 0.0, w.dt, 1)
         start = time.perf_counter()
         for _ in range(steps):
-            x = o.lsrk4(x, 0.0, ws.dt, 1)
+            x = o.lsrk4(x, 0.0, w.dt, 1)
         el = time.perf_counter() - start
         dofs = 6 * o.asm.N * o.asm.K
         v = dofs * steps / el
-        sample = ("each step: one LSRK4 step of the oracle on the jittered-sphere workload "
-                  "at 4^3 (384 elements, p=3), assembly excluded")
+        sample = ("each step: one LSRK4 step (dt of the 32^3 workload) of the oracle on the "
+                  "jittered-sphere workload at %d^3 (%d elements, p=3), assembly excluded; "
+                  "sparse operator product on %d PyTorch CPU threads"
+                  % (n_ref, o.asm.K, torch.get_num_threads()))
+        ref_config = dict(config)
+        ref_config.update(
+            workload="jittered_sphere sample: %d^3 Kuhn grid of [0,1]^3 (+-0.15h jitter), %d "
+                     "tets, p=3, eps=4 sphere r=0.25, upwind, LSRK4 (the oracle's bounded "
+                     "sample of the %d^3 workload)" % (n_ref, o.asm.K, args.n),
+            K=o.asm.K, l2="oracle on the host CPU")
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
                 "steps": steps, "warmup": warm, "ms_per_step": el * 1e3 / steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic", "config": config,
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": sample},
+                "dtype": "f64", "data": "synthetic", "config": ref_config,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+                                 "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -665,8 +763,9 @@ def main():
                                         "state, FP64 gradient, sqrt(N) checkpoints",
                                **run_adjoint(args.adjoint_steps, args.adjoint_n))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base, _ = cpu_reference(seconds_budget=15.0)
+        base, sphere, dipole = cpu_reference()
         line["cpu_baseline"] = base
+        line["accuracy_vs_oracle"] = replica_accuracy(sphere, dipole)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -247,7 +247,9 @@ int dgm_advance_host(dgm_plan* plan, const void* fields_in, void* fields_out,
 
 /* Discrete energy 1/2 (e . M_eps e + h . M_mu h) per column, accumulated in
  * FP64 (Sec. III, energy conservation of the central flux).  out: host [S].
- * Synchronises the stream. */
+ * Synchronises the stream.  A non-finite energy (a NaN or an overflow in the
+ * column's state) latches DGM_ENAN in the device status word and the call
+ * returns DGM_ENAN (out still holds the energies). */
 int dgm_energy(dgm_plan* plan, const void* fields, double* out);
 
 /* Element ids of the PML elements in auxiliary-buffer order (ascending):

@@ -267,8 +267,7 @@ class Assembly:
         out = np.empty_like(y)
         for bi in range(self.nblk):
             blk = y[bi * R * n3:(bi + 1) * R * n3].reshape(R, n3, -1)
-            out[bi * R * n3:(bi + 1) * R * n3] = np.einsum(
-                "kij,kjs->kis", self.Minv[bi], blk).reshape(R * n3, -1)
+            out[bi * R * n3:(bi + 1) * R * n3] = np.matmul(self.Minv[bi], blk).reshape(R * n3, -1)
         return out
 
     def energy(self, x):

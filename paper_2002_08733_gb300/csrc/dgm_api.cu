@@ -138,12 +138,16 @@ energy_partial(const R* __restrict__ u, const double* __restrict__ geo, int64_t 
     if (threadIdx.x == 0) part[int64_t(s) * gridDim.x + blockIdx.x] = red[0];
 }
 
-__global__ void energy_final(const double* __restrict__ part, int nblk, int S, double* __restrict__ out) {
+// Final sum per column; a non-finite energy (a NaN or an overflow anywhere in
+// the column's state) latches ST_NAN in the plan's device status word.
+__global__ void energy_final(const double* __restrict__ part, int nblk, int S, double* __restrict__ out,
+                             int32_t* status) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     double acc = 0.0;
     for (int b = 0; b < nblk; ++b) acc += part[int64_t(s) * nblk + b];
     out[s] = acc;
+    if (!isfinite(acc)) atomicOr(status, int32_t(ST_NAN));
 }
 
 // E at receiver points: out[s][r][c] = sum_{j,l} W_r[c][j N + l] u[(j N + l)][e_r S + s],
@@ -610,13 +614,18 @@ int dgm_energy(dgm_plan* P, const void* fields, double* out) {
     else
         energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
             static_cast<const float*>(fields), geo, P->mesh.K, Sc, P->N, part);
-    energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(part, ENERGY_BLOCKS, Sc, res);
+    energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(
+        part, ENERGY_BLOCKS, Sc, res, reinterpret_cast<int32_t*>(P->geom + P->off_status));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
     e = cudaMemcpyAsync(out, res, sizeof(double) * Sc, cudaMemcpyDeviceToHost, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "energy copy");
     e = cudaStreamSynchronize(P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "energy sync");
+    for (int s = 0; s < Sc; ++s)
+        if (!std::isfinite(out[s]))
+            return fail(DGM_ENAN, "non-finite energy in column " + std::to_string(s) +
+                                      " (latched in the device status word)");
     return DGM_OK;
 }
 
@@ -760,7 +769,8 @@ extern "C" int dgm_energy_noalloc(dgm_plan* P, const void* fields, double* out_d
     else
         energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
             static_cast<const float*>(fields), geo, P->mesh.K, Sc, P->N, part);
-    energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(part, ENERGY_BLOCKS, Sc, out_device);
+    energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(
+        part, ENERGY_BLOCKS, Sc, out_device, reinterpret_cast<int32_t*>(P->geom + P->off_status));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
     return DGM_OK;

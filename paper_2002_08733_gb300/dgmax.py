@@ -270,9 +270,32 @@ class Solver(Plan):
 
     def energy_noalloc(self, out, fields=None):
         """Allocation-free energy into the device tensor `out` (S doubles) on the
-        bound stream; the library's own fixed scratch array holds the partial sums."""
+        bound stream; the library's own fixed scratch array holds the partial sums.
+
+        `out` must be a contiguous float64 CUDA tensor on the plan's device with
+        at least S elements: the kernel writes it directly, so anything else is
+        rejected here, before the library is called."""
+        self._check_device_tensor(out, self.torch.float64, self.S, "out")
         f = self.fields[self.current()] if fields is None else fields
+        self._check_device_tensor(f, self.dtype, 6 * self.N * self.K * self.S, "fields")
         _check(_lib.dgm_energy_noalloc(self.handle, _ptr(f), _ptr(out)))
+
+    def _check_device_tensor(self, t, dtype, min_numel, name):
+        """A buffer the kernels read or write directly: a contiguous torch tensor
+        of `dtype` on this plan's CUDA device with at least `min_numel` elements."""
+        torch = self.torch
+        if not torch.is_tensor(t):
+            raise ValueError("%s must be a torch tensor on %s, got %s" % (name, self.device,
+                                                                          type(t).__name__))
+        if not t.is_cuda or t.device.index != self.device.index:
+            raise ValueError("%s must live on %s, got %s" % (name, self.device, t.device))
+        if t.dtype != dtype:
+            raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.numel() < min_numel:
+            raise ValueError("%s needs at least %d elements, got %d" % (name, min_numel,
+                                                                         t.numel()))
 
     def project(self, fn, column=0):
         """L2 projection of fn(points [n,3]) -> [n,6] (E, H) into the current state."""

@@ -112,3 +112,48 @@ def test_invalid_inputs_are_rejected(lib, case):
     codes = {"repeated": 2, "range": 2, "degenerate": 2, "nonmanifold": 2, "eps": 1,
              "order": 3, "leapfrog_upwind": 3, "dt": 1, "columns": 1, "empty": 1}
     assert ei.value.code == codes[case]
+
+
+def test_energy_noalloc_rejects_bad_output_buffers(lib, monkeypatch):
+    """The allocation-free energy writes its output buffer from a kernel, so the
+    binding checks it before the call: a numpy array, a CPU tensor, an FP32
+    tensor, a short tensor or a non-contiguous one never reach the library."""
+    import torch
+    from paper_2002_08733_gb300 import dgmax as D
+
+    class FakeCuda:
+        """Stands in for a CUDA tensor: only the attributes the check reads."""
+        def __init__(self, dtype, numel, index=0, contiguous=True):
+            self.dtype, self._n, self._c = dtype, numel, contiguous
+            self.is_cuda = True
+            self.device = torch.device("cuda", index)
+
+        def numel(self):
+            return self._n
+
+        def is_contiguous(self):
+            return self._c
+
+    calls = []
+
+    class NoLib:
+        def __getattr__(self, name):
+            calls.append(name)
+            raise AssertionError("library called: " + name)
+
+    monkeypatch.setattr(D, "_lib", NoLib())
+    g = D.Solver.__new__(D.Solver)
+    g.torch, g.device, g.S, g.N, g.K = torch, torch.device("cuda", 0), 4, 4, 6
+    g.dtype = torch.float32
+    g.fields = [FakeCuda(torch.float32, 6 * 4 * 6 * 4)] * 2
+    g.current = lambda: 0
+    monkeypatch.setattr(torch, "is_tensor", lambda t: isinstance(t, (torch.Tensor, FakeCuda)))
+    bad = [np.zeros(4), torch.zeros(4, dtype=torch.float64), FakeCuda(torch.float32, 4),
+           FakeCuda(torch.float64, 3), FakeCuda(torch.float64, 4, contiguous=False),
+           FakeCuda(torch.float64, 4, index=1)]
+    for out in bad:
+        with pytest.raises(ValueError):
+            g.energy_noalloc(out)
+    with pytest.raises(ValueError):   # fields of the wrong precision
+        g.energy_noalloc(FakeCuda(torch.float64, 4), fields=FakeCuda(torch.float64, 6 * 96))
+    assert calls == []

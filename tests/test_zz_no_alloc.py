@@ -49,3 +49,38 @@ def test_noalloc_energy_rejects_too_many_columns(D):
     with pytest.raises(D.DgmError) as ei:
         g.energy_noalloc(out)
     assert ei.value.code == 1 and "at most 64 columns" in str(ei.value)
+
+
+def test_noalloc_energy_at_the_column_limit(D):
+    """A plan with exactly DGM_NOALLOC_MAX_COLUMNS (64) columns uses every entry
+    of the fixed scratch array; it matches dgm_energy on two calls in a row."""
+    import torch
+    xyz, tets = W.kuhn_mesh(2, jitter=0.1, seed=45)
+    K, p, S = len(tets), 2, 64
+    g = D.Solver(xyz, tets, 1.3, 0.8, p, "fp64", "upwind", "lsrk4", 1e-3, S=S)
+    for call, seed in enumerate((46, 47)):
+        g.set_state(W.random_state(K, S, p, seed=seed))
+        want = g.energy()
+        out = torch.full((S,), float("nan"), dtype=torch.float64, device=g.device)
+        g.energy_noalloc(out)
+        torch.cuda.synchronize(g.device)
+        got = out.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), call
+
+
+def test_noalloc_energy_allocates_no_device_memory(D):
+    """After a first call (which looks up the scratch array's address), many
+    calls leave the device's free memory unchanged: no allocation happens."""
+    import torch
+    xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=48)
+    K, p, S = len(tets), 3, 8
+    g = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", 1e-3, S=S)
+    g.set_state(W.random_state(K, S, p, seed=49))
+    out = torch.zeros(S, dtype=torch.float64, device=g.device)
+    g.energy_noalloc(out)
+    torch.cuda.synchronize(g.device)
+    free0 = torch.cuda.mem_get_info(g.device)[0]
+    for _ in range(200):
+        g.energy_noalloc(out)
+    torch.cuda.synchronize(g.device)
+    assert torch.cuda.mem_get_info(g.device)[0] == free0
