@@ -41,10 +41,11 @@ import workloads as W  # noqa: E402
 METRIC = "DoF-updates/s"
 # FP32 LSRK stage-kernel variants in autotuner order (degree 3 instantiations)
 VARIANT_NAMES = ["32 cols x 384 thr", "32 cols x 192 thr", "16 cols x 192 thr",
-                 "64 cols paired x 384 thr, packed FP32x2", "64 cols paired x 384 thr, scalar"]
+                 "64 cols paired x 384 thr, packed FP32x2", "64 cols paired x 384 thr, scalar",
+                 "64 cols x 512 thr, curl and lift on tensor cores (tcgen05, 3xTF32)"]
 KERNEL_NAMES = ["stage_kernel<3,float,32,384,LSRK>", "stage_kernel<3,float,32,192,LSRK>",
                 "stage_kernel<3,float,16,192,LSRK>", "stage2_kernel<3,F2x,384>",
-                "stage2_kernel<3,P2,384>"]
+                "stage2_kernel<3,P2,384>", "stage_kernel<3,float,64,512,LSRK,TC>"]
 UNIT = "DoF-updates/s"
 
 
@@ -53,7 +54,7 @@ def kernel_name(variant, K, N, S):
     arithmetic when every index fits (the library's own test: field and
     face-jump rows x columns, geometry, per-face table below 2^32)."""
     name = KERNEL_NAMES[variant]
-    if variant < 3:
+    if variant < 3 or variant == 5:
         NF = {4: 3, 10: 6, 20: 10, 35: 15, 56: 21}[N]
         C = K * S
         fits = max(6 * N * C, 24 * NF * C, 16 * K, 52 * K) < 2 ** 32

@@ -289,6 +289,72 @@ int dgm_project(dgm_plan* plan, const double* samples, int32_t column, void* fie
 #define DGM_NOALLOC_MAX_COLUMNS 64
 int dgm_energy_noalloc(dgm_plan* plan, const void* fields, double* out_device);
 
+/* ---- One mesh on several GPUs: element partitions with a halo exchange ----
+ *
+ * The right-hand side of an element (Secs. III-IV: volume curl, face traces,
+ * numerical flux, lift, mass inverse) reads only its own coefficients and
+ * those of its face neighbours.  A part of the mesh therefore advances on its
+ * own GPU if, before every stage, it holds current copies of the
+ * coefficients of the other parts' elements that share a face with it (its
+ * halo).  The library partitions, builds the halo lists, packs and unpacks
+ * halo coefficients and runs single stages; moving the packed buffers between
+ * GPUs (NCCL send/receive, or a copy into the receiver's own memory) is the
+ * caller's. */
+
+/* Slab partition: elements sorted by centroid coordinate along `axis` (0, 1,
+ * 2; ties by element id) and cut into nparts contiguous runs of nearly equal
+ * size (k-plane slabs on a Kuhn grid).  part: host [nt] part ids.  No CUDA
+ * call.  Errors: DGM_EINVAL, DGM_EMESH. */
+int dgm_partition_slabs(int64_t nv, const double* xyz, int64_t nt, const int64_t* tets,
+                        int32_t axis, int32_t nparts, int32_t* part);
+
+typedef struct {
+    int64_t n_owned;   /* elements of this part */
+    int64_t n_ghost;   /* other parts' elements that share a face with this part */
+    int64_t n_send;    /* total entries of send_idx (an element may go to two peers) */
+    int64_t n_recv;    /* total entries of recv_idx (= n_ghost) */
+    int32_t n_peers;   /* parts this part exchanges with */
+    int32_t reserved;
+} dgm_halo_sizes;
+
+/* Local numbering and halo lists of part `rank` of a partition (part[nt]):
+ * local element i < n_owned is the i-th owned element in ascending global
+ * id, local element n_owned + j the j-th ghost in ascending global id
+ * (local_to_global: [n_owned + n_ghost]).  Per peer q (peers[n_peers],
+ * ascending): send_idx holds send_count[q] local ids of owned elements whose
+ * coefficients peer q needs, recv_idx recv_count[q] local ids of the ghosts
+ * peer q owns, both in ascending global id, so that a part's send list to q
+ * and q's receive list from it match entry by entry; lists are stored peer
+ * after peer.  With local_to_global NULL only *sizes is filled.  All arrays
+ * are host memory, caller-owned.  No CUDA call. */
+int dgm_halo_build(int64_t nt, const int64_t* tets, const int32_t* part, int32_t nparts,
+                   int32_t rank, dgm_halo_sizes* sizes, int64_t* local_to_global,
+                   int32_t* peers, int64_t* send_count, int64_t* send_idx,
+                   int64_t* recv_count, int64_t* recv_idx);
+
+/* Only the first n elements of the plan are updated by the stage kernels
+ * (dgm_rhs, dgm_stage, dgm_advance, dgm_autotune) and summed by dgm_energy;
+ * the others are halo copies that the caller keeps current.  1 <= n <= K
+ * (default K).  Plans with fewer active elements reject the adjoint and
+ * the batch.  No CUDA call. */
+int dgm_set_active(dgm_plan* plan, int64_t n);
+
+/* Gather the coefficients of n elements (local ids idx_device[n], int64,
+ * device) of the field buffer `fields` into buf_device [6N][n][S] (real
+ * numbers of the plan's precision, device), or scatter them back
+ * (unpack).  Asynchronous on the bound stream. */
+int dgm_halo_pack(dgm_plan* plan, const void* fields, const int64_t* idx_device, int64_t n,
+                  void* buf_device);
+int dgm_halo_unpack(dgm_plan* plan, void* fields, const int64_t* idx_device, int64_t n,
+                    const void* buf_device);
+
+/* One stage k (0..4) of the LSRK4 step that starts at time t: reads the
+ * current field (and auxiliary) buffer, writes the other one and the
+ * residuals, and makes it current (dgm_current).  Five calls with k = 0..4
+ * equal dgm_advance(plan, 1, t); between them a partitioned run refreshes
+ * the halo of the new current buffer.  Asynchronous. */
+int dgm_stage(dgm_plan* plan, int32_t k, double t);
+
 /* Read and clear the device status word (synchronises).  Returns DGM_OK or
  * the latched device error. */
 int dgm_status_check(dgm_plan* plan);

@@ -52,6 +52,74 @@ constexpr int ENERGY_THREADS = 256;
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Bytes of the tensor-core variant's operator image for degree p (0: no variant).
+static size_t tc_image_bytes(int p) {
+    switch (p) {
+        case 2: return TcShape<2>::B_BYTES;
+        case 3: return TcShape<3>::B_BYTES;
+        default: return 0;
+    }
+}
+
+// x rounded to the nearest TF32 value (11 significant bits), as a float
+static float tf32_nearest(double x) {
+    if (x == 0.0 || !std::isfinite(x)) return float(x);
+    int ex;
+    const double m = std::frexp(x, &ex);   // x = m 2^ex, 0.5 <= |m| < 1
+    return float(std::ldexp(std::round(std::ldexp(m, 11)), ex - 11));
+}
+
+// The operator image of the tensor-core stage variant (TcShape): the reference
+// curl B_curl[(i, m)][(j, l)] = eps_jai S_a[l][m] (Eq. (matrix_free_curl)) and
+// the lift B_lift[(f, m)][l] = R_f[m][l] (Eqs. (uwc)/(cwc)), each as TF32 hi
+// and lo parts (hi = tf32(x), lo = tf32(x - hi)) in the K-major core-matrix
+// layout of tc_b_offset.  Entries below 1e-13 of the matrix maximum are the
+// round-off of exact zeros and are dropped, as in the compiled operators.
+template <int P>
+static void build_tc_image_p(const std::vector<double>& S, const std::vector<double>& R,
+                             std::vector<unsigned char>& out) {
+    using TS = TcShape<P>;
+    constexpr int N = TS::N, NF = TS::NF;
+    out.assign(TS::B_BYTES, 0);
+    double smax = 0, rmax = 0;
+    for (double v : S) smax = std::fmax(smax, std::fabs(v));
+    for (double v : R) rmax = std::fmax(rmax, std::fabs(v));
+    auto put = [&](size_t base, int n, int k, int K, float v) {
+        std::memcpy(out.data() + base + tc_b_offset(n, k, K), &v, sizeof(float));
+    };
+    auto split = [&](size_t hi_base, size_t lo_base, int n, int k, int K, double x) {
+        const float hi = tf32_nearest(x);
+        put(hi_base, n, k, K, hi);
+        put(lo_base, n, k, K, tf32_nearest(x - double(hi)));
+    };
+    for (int i = 0; i < 3; ++i)          // input component
+        for (int j = 0; j < 3; ++j) {    // output component
+            if (i == j) continue;
+            const int a = 3 - i - j;     // curl_j = eps_jai d_a v_i
+            const double eps = ((j - a + 3) % 3 == 2) ? 1.0 : -1.0;   // eps_jai with (j, a, i) a permutation
+            for (int m = 0; m < N; ++m)
+                for (int l = 0; l < N; ++l) {
+                    double v = S[(size_t(a) * N + l) * N + m];
+                    if (!(std::fabs(v) > 1e-13 * smax)) continue;
+                    split(0, TS::B_CURL, j * N + l, i * N + m, TS::KC, eps * v);
+                }
+        }
+    for (int f = 0; f < 4; ++f)
+        for (int m = 0; m < NF; ++m)
+            for (int l = 0; l < N; ++l) {
+                const double v = R[(size_t(f) * NF + m) * N + l];
+                if (!(std::fabs(v) > 1e-13 * rmax)) continue;
+                split(2 * TS::B_CURL, 2 * TS::B_CURL + TS::B_LIFT, l, f * NF + m, TS::KL, v);
+            }
+}
+
+static void build_tc_image(int p, const std::vector<double>& S, const std::vector<double>& R,
+                           std::vector<unsigned char>& out) {
+    if (p == 2) build_tc_image_p<2>(S, R, out);
+    else if (p == 3) build_tc_image_p<3>(S, R, out);
+    else out.clear();
+}
+
 }  // namespace dgm
 
 using namespace dgm;
@@ -65,7 +133,8 @@ struct dgm_plan {
     bool has_pml = false;
     // geometry buffer layout (byte offsets)
     size_t off_geo = 0, off_nbr = 0, off_pml = 0, off_src = 0, off_part = 0, off_status = 0,
-           off_rec = 0, off_time = 0, off_geo32 = 0, off_fnb = 0, off_fnb32 = 0, bytes_geom = 0;
+           off_rec = 0, off_time = 0, off_geo32 = 0, off_fnb = 0, off_fnb32 = 0, off_tcb = 0,
+           bytes_tcb = 0, bytes_geom = 0;
     int n_rec = 0;
     std::vector<double> src_host;   // S * (SRC_HDR + 3N)
     bool have_src = false;
@@ -82,6 +151,7 @@ struct dgm_plan {
     int variant = 0;          // LSRK stage tile shape chosen by dgm_autotune
     int force_index64 = 0;    // dgm_set_index64
     int tile_groups = 1;      // tile visiting order (dgm_autotune, dgm_set_tile_groups)
+    int64_t k_active = 0;     // elements updated (dgm_set_active); the rest are halo copies
     float variant_ms[8] = {0};
 };
 
@@ -96,17 +166,21 @@ static int cuda_fail(cudaError_t e, const char* what) {
     return fail(DGM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+namespace dgm {
+int partition_fail(int code, const std::string& msg) { return fail(code, msg); }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 energy: W_s = 1/2 sum_T |det| sum_l (eps u_l^T G u_l + mu h_l^T G h_l), G = A^-1 A^-T
 template <typename R>
 __global__ void __launch_bounds__(ENERGY_THREADS)
-energy_partial(const R* __restrict__ u, const double* __restrict__ geo, int64_t K, int S, int N,
-               double* __restrict__ part) {
+energy_partial(const R* __restrict__ u, const double* __restrict__ geo, int64_t K, int64_t Kact,
+               int S, int N, double* __restrict__ part) {
     __shared__ double red[ENERGY_THREADS];
     const int s = blockIdx.y;
     const int64_t C = K * S;
     double acc = 0.0;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < K;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < Kact;
          e += int64_t(gridDim.x) * blockDim.x) {
         double a[9];
         for (int k = 0; k < 9; ++k) a[k] = geo[int64_t(G_AIT + k) * K + e];
@@ -259,7 +333,12 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
     }
     P->off_rec = off;
     off = align256(off + sizeof(double) * size_t(opt->max_receivers) * (REC_HDR + 9 * P->N));
+    // operator image of the tensor-core stage variant (FP32, p = 2, 3)
+    P->bytes_tcb = opt->precision == DGM_FP32 ? tc_image_bytes(opt->p) : 0;
+    P->off_tcb = off;
+    off = align256(off + P->bytes_tcb);
     P->bytes_geom = off;
+    P->k_active = K;
     P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
     for (int s = 0; s < Sc; ++s) P->src_host[size_t(s) * (SRC_HDR + 3 * P->N)] = -1.0;
     *out = P;
@@ -364,6 +443,13 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
         return cuda_fail(e, "upload sources");
     if ((e = cudaMemsetAsync(P->geom + P->off_status, 0, 64, st)) != cudaSuccess)
         return cuda_fail(e, "clear status");
+    std::vector<unsigned char> tcimg;
+    if (P->bytes_tcb) {
+        build_tc_image(P->opt.p, P->S, P->R, tcimg);
+        if ((e = cudaMemcpyAsync(P->geom + P->off_tcb, tcimg.data(), tcimg.size(),
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "upload tensor-core operator image");
+    }
     if (int rc = build_face_table(P)) return rc;
     // the host copies above are pageable: finish them before the host vectors can change
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
@@ -390,6 +476,8 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.variant = P->variant;
     prm.force_index64 = P->force_index64;
     prm.tile_groups = P->tile_groups;
+    prm.tc_b = P->bytes_tcb ? static_cast<const void*>(P->geom + P->off_tcb) : nullptr;
+    prm.K_active = P->k_active;
 }
 
 int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double* pos,
@@ -583,6 +671,88 @@ int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
 
 int dgm_current(const dgm_plan* P) { return P ? P->cur : -1; }
 
+int dgm_stage(dgm_plan* P, int32_t k, double t) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (P->opt.integrator != DGM_LSRK4) return fail(DGM_ESTATE, "dgm_stage needs an LSRK4 plan");
+    if (k < 0 || k > 4) return fail(DGM_EINVAL, "stage index must be 0..4");
+    StageParams prm;
+    stage_params(P, prm);
+    const double dt = P->opt.dt;
+    prm.u = P->fields[P->cur];
+    prm.u_out = P->fields[1 - P->cur];
+    prm.res = P->res;
+    prm.aux = P->aux[P->cur];
+    prm.aux_out = P->aux[1 - P->cur];
+    prm.aux_res = P->aux_res;
+    prm.t = t + LSRK_C[k] * dt;
+    prm.a = LSRK_A[k];
+    prm.b = LSRK_B[k];
+    int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+    if (rc) return fail(rc, "stage kernel launch failed");
+    P->cur = 1 - P->cur;
+    return DGM_OK;
+}
+
+int dgm_set_active(dgm_plan* P, int64_t n) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (n < 1 || n > P->mesh.K) return fail(DGM_EINVAL, "active element count must be in 1..K");
+    P->k_active = n;
+    return DGM_OK;
+}
+
+}  // extern "C"
+
+// Halo copies: buf[(r n + i) S + s] <-> fields[(r K + idx[i]) S + s], r = c N + l.
+// An element id outside 0..K-1 is skipped and latched as ST_BAD_INDEX.
+template <typename R>
+__global__ void halo_copy(R* __restrict__ fields, const int64_t* __restrict__ idx, int64_t n,
+                          int64_t K, int S, int rows, R* __restrict__ buf, int to_buf,
+                          int32_t* status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t per = n * S;
+    if (i >= per * rows) return;
+    const int64_t r = i / per, rem = i - r * per;
+    const int64_t j = rem / S;
+    const int s = int(rem - j * S);
+    const int64_t e = idx[j];
+    if (e < 0 || e >= K) {
+        atomicOr(status, int32_t(ST_BAD_INDEX));
+        return;
+    }
+    const int64_t g = (r * K + e) * S + s;
+    if (to_buf) buf[i] = fields[g];
+    else fields[g] = buf[i];
+}
+
+static int halo_copy_launch(dgm_plan* P, void* fields, const int64_t* idx, int64_t n, void* buf,
+                            int to_buf) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (n < 0 || (n > 0 && (!fields || !idx || !buf))) return fail(DGM_EINVAL, "null halo argument");
+    if (n == 0) return DGM_OK;
+    const int rows = 6 * P->N, S = P->opt.n_columns;
+    const int64_t total = n * S * rows;
+    const unsigned grid = unsigned((total + 255) / 256);
+    int32_t* status = reinterpret_cast<int32_t*>(P->geom + P->off_status);
+    if (P->kt->real_size == 8)
+        halo_copy<double><<<grid, 256, 0, P->stream>>>(static_cast<double*>(fields), idx, n, P->mesh.K,
+                                                        S, rows, static_cast<double*>(buf), to_buf, status);
+    else
+        halo_copy<float><<<grid, 256, 0, P->stream>>>(static_cast<float*>(fields), idx, n, P->mesh.K, S,
+                                                       rows, static_cast<float*>(buf), to_buf, status);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "halo copy");
+}
+
+extern "C" {
+
+int dgm_halo_pack(dgm_plan* P, const void* fields, const int64_t* idx, int64_t n, void* buf) {
+    return halo_copy_launch(P, const_cast<void*>(fields), idx, n, buf, 1);
+}
+
+int dgm_halo_unpack(dgm_plan* P, void* fields, const int64_t* idx, int64_t n, const void* buf) {
+    return halo_copy_launch(P, fields, idx, n, const_cast<void*>(buf), 0);
+}
+
 int dgm_advance_host(dgm_plan* P, const void* fields_in, void* fields_out, int64_t n_steps, double t0) {
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (!fields_in || !fields_out) return fail(DGM_EINVAL, "null host buffer");
@@ -610,10 +780,10 @@ int dgm_energy(dgm_plan* P, const void* fields, double* out) {
     dim3 grid(ENERGY_BLOCKS, Sc);
     if (P->kt->real_size == 8)
         energy_partial<double><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const double*>(fields), geo, P->mesh.K, Sc, P->N, part);
+            static_cast<const double*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
     else
         energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const float*>(fields), geo, P->mesh.K, Sc, P->N, part);
+            static_cast<const float*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
     energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(
         part, ENERGY_BLOCKS, Sc, res, reinterpret_cast<int32_t*>(P->geom + P->off_status));
     cudaError_t e = cudaGetLastError();
@@ -709,6 +879,7 @@ int dgm_status_check(dgm_plan* P) {
     if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "status sync");
     if (st & ST_TIMEOUT) return fail(DGM_ETIMEOUT, "a device-side wait gave up");
     if (st & ST_NAN) return fail(DGM_ENAN, "non-finite values detected");
+    if (st & ST_BAD_INDEX) return fail(DGM_EINVAL, "halo element id out of range (skipped)");
     if (st & ST_BAD_NEIGHBOUR) return fail(DGM_EMESH, "out-of-range neighbour index on the device");
     return DGM_OK;
 }
@@ -765,10 +936,10 @@ extern "C" int dgm_energy_noalloc(dgm_plan* P, const void* fields, double* out_d
     dim3 grid(ENERGY_BLOCKS, Sc);
     if (P->kt->real_size == 8)
         energy_partial<double><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const double*>(fields), geo, P->mesh.K, Sc, P->N, part);
+            static_cast<const double*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
     else
         energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const float*>(fields), geo, P->mesh.K, Sc, P->N, part);
+            static_cast<const float*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
     energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(
         part, ENERGY_BLOCKS, Sc, out_device, reinterpret_cast<int32_t*>(P->geom + P->off_status));
     e = cudaGetLastError();
@@ -833,6 +1004,8 @@ extern "C" int dgm_batch_create(dgm_batch** out, dgm_plan* const* members, int32
     for (int i = 0; i < n; ++i) {
         if (!members[i] || !members[i]->bound) return fail(DGM_EINVAL, "batch member not bound");
         if (members[i]->opt.integrator != DGM_LSRK4) return fail(DGM_EINVAL, "batch members must use LSRK4");
+        if (members[i]->k_active < members[i]->mesh.K)
+            return fail(DGM_EINVAL, "batch members must have every element active (no halo)");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(DGM_EINVAL, "duplicate batch member");
     }
@@ -1046,6 +1219,7 @@ static int copy_state(dgm_plan* P, StateRef dst, const void* f, const void* a, c
 }
 
 extern "C" int dgm_forward_record(dgm_plan* P, int64_t n_steps, double t0, double* records, void* ws_) {
+    if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (P->opt.integrator != DGM_LSRK4) return fail(DGM_EUNSUP, "the adjoint needs LSRK4");
     if (!records || !ws_ || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
@@ -1110,6 +1284,7 @@ static int axpby(dgm_plan* P, StateRef y, StateRef x, double a, double b, const 
 
 extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double* drec, void* ws_,
                            double* deps, double* dmu) {
+    if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (!drec || !ws_ || !deps || !dmu || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
     if (reinterpret_cast<uintptr_t>(ws_) % 256) return fail(DGM_EINVAL, "workspace must be 256-byte aligned");

@@ -16,6 +16,45 @@ constexpr int PMAX = 5;
 __host__ __device__ constexpr int nmodes(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 __host__ __device__ constexpr int nfmodes(int p) { return (p + 1) * (p + 2) / 2; }
 
+__host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Shapes of the tensor-core variant of the FP32 stage kernel (p = 2, 3; 64
+// columns per CTA; tensor-memory row = (column, field)).  Per row the
+// pre-mass right-hand side of one field is
+//   D = A_swap B_curl + sum_j A_g,j B_lift
+// with A_swap = +-sign(det A) times the other field's coefficients (K = 3N,
+// index i N + m for component i, mode m), B_curl[(i, m)][(j, l)] =
+// eps_jai S_a[l][m] (the reference curl of Eq. (matrix_free_curl)), A_g,j the
+// pulled-back face fluxes of component j (K = 4 NF, index f NF + m) and
+// B_lift[(f, m)][l] = R_f[m][l] (the lift of Eqs. (uwc)/(cwc)).  Component j's
+// lift lands in D columns [j N, j N + NL), which overlap the next component's
+// first columns only where B_lift has zero padding.
+template <int P>
+struct TcShape {
+    static constexpr int N = nmodes(P), NF = nfmodes(P);
+    static constexpr int KC = round_up(3 * N, 8);     // curl: K (TF32 steps of 8)
+    static constexpr int NC = round_up(3 * N, 16);    // curl: N (multiple of 16 at M = 128)
+    static constexpr int KL = round_up(4 * NF, 8);    // lift: K per component
+    static constexpr int NL = round_up(N, 16);        // lift: N per component
+    static constexpr int ND = NC > 2 * N + NL ? NC : 2 * N + NL;   // D columns touched
+    // tensor-memory columns: A_swap hi/lo, A_g hi/lo (3 components each), D
+    static constexpr int T_SWAP_HI = 0, T_SWAP_LO = KC;
+    static constexpr int T_G_HI = 2 * KC, T_G_LO = 2 * KC + 3 * KL;
+    static constexpr int T_D = round_up(2 * KC + 6 * KL, 32);
+    static constexpr int TCOLS = 512;
+    static constexpr bool FITS = T_D + ND <= TCOLS;   // tensor-memory budget
+    // B image (bytes, K-major core matrices): curl hi, curl lo, lift hi, lift lo
+    static constexpr int B_CURL = NC * KC * 4, B_LIFT = NL * KL * 4;
+    static constexpr int B_BYTES = 2 * B_CURL + 2 * B_LIFT;
+    static constexpr int SBO_CURL = KC * 32, SBO_LIFT = KL * 32;   // bytes per 8-row group
+};
+
+// byte offset of entry (n, k) of a K-major, no-swizzle B operand with K columns
+// per row: 8-row x 4-value core matrices, K-adjacent ones contiguous
+__host__ __device__ constexpr int tc_b_offset(int n, int k, int K) {
+    return (n / 8) * (K * 32) + (k / 4) * 128 + (n % 8) * 16 + (k % 4) * 4;
+}
+
 // Per-element FP64 record, stored structure-of-arrays: geo[k * K + e].
 enum GeoSlot {
     G_AIT = 0,    // 9 entries of A^-T, row major
@@ -40,7 +79,7 @@ constexpr int SRC_HDR = 8;
 
 enum Mode { MODE_RHS = 0, MODE_LSRK = 1, MODE_LF_E = 2, MODE_LF_H = 3, MODE_RAW = 4 };
 
-enum StatusBits { ST_OK = 0, ST_BAD_NEIGHBOUR = 1, ST_NAN = 2, ST_TIMEOUT = 4 };
+enum StatusBits { ST_OK = 0, ST_BAD_NEIGHBOUR = 1, ST_NAN = 2, ST_TIMEOUT = 4, ST_BAD_INDEX = 8 };
 
 struct StageParams {
     const void* u;        // fields in  [6][N][K][S]
@@ -68,6 +107,8 @@ struct StageParams {
     int32_t variant;      // tile-shape variant of the LSRK stage kernel (autotuner)
     int32_t force_index64;// 1: 64-bit index arithmetic even where 32 bits suffice
     int32_t tile_groups;  // tile visiting order: G interleaved segments (1: in order)
+    const void* tc_b;     // tensor-core variant: B operand image (TcShape<P>::B_BYTES), or null
+    int64_t K_active;     // elements updated: the first K_active (the rest are halo copies)
 };
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms

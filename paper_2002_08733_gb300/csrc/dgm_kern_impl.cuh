@@ -25,6 +25,11 @@ constexpr int kP = DGM_P;
 using Real = DGM_REAL;
 // tile shape: columns per CTA and threads per CTA (DGM_TE / DGM_NT select an
 // autotuner variant; the defaults are the shapes measured best at p = 3)
+#ifdef DGM_TC
+constexpr bool kTC = true;    // tensor-core variant (curl and lift on tcgen05)
+#else
+constexpr bool kTC = false;
+#endif
 #ifdef DGM_TE
 constexpr int kTE = DGM_TE;
 constexpr int kNT = DGM_NT;
@@ -98,7 +103,7 @@ bool fits_32bit(const StageParams& p) {
 }
 
 int launch_mode(const StageParams& prm, cudaStream_t st) {
-    const int64_t C = prm.K * prm.S;
+    const int64_t C = prm.K_active * prm.S;   // columns updated
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + 63) / 64);
     StageParams q = prm;
@@ -111,9 +116,10 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
 #else
 template <typename IX>
 int launch_ix(const StageParams& q, unsigned grid, cudaStream_t st) {
-    constexpr size_t smem = stage_smem_bytes<kP, Real, kTE>();
+    constexpr size_t smem = stage_smem_bytes<kP, Real, kTE, kTC>();
     static bool configured = false;
-    auto k = stage_kernel<kP, Real, kTE, kNT, DGM_MODE, IX>;
+    auto k = stage_kernel<kP, Real, kTE, kNT, DGM_MODE, IX, kTC>;
+    if (kTC && q.tc_b == nullptr) return DGM_EUNSUP;   // no operator image for this plan
     if (!configured) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
             cudaSuccess)
@@ -136,7 +142,7 @@ bool fits_32bit(const StageParams& p) {
 }
 
 int launch_mode(const StageParams& prm, cudaStream_t st) {
-    const int64_t C = prm.K * prm.S;
+    const int64_t C = prm.K_active * prm.S;   // columns updated
     if (C <= 0) return DGM_OK;
     const unsigned grid = unsigned((C + kTE - 1) / kTE);
     StageParams q = prm;

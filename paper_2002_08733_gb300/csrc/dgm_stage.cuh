@@ -45,6 +45,7 @@
 
 #include "dgm_internal.h"
 #include "dgm_ops_gen.cuh"
+#include "dgm_tc.cuh"
 
 namespace dgm {
 
@@ -90,10 +91,11 @@ enum FaceConstRef {
 };
 constexpr int GM = 6;    // metric A^T A per column: entries 00, 01, 02, 11, 12, 22
 
-template <int P, typename R, int TE>
+template <int P, typename R, int TE, bool TC = false>
 __host__ __device__ constexpr size_t stage_smem_bytes() {
-    return sizeof(R) * size_t(TE) *
-           (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FGR + EG + GM + NBS);
+    // tensor-core variant: + B operand image, an mbarrier and the tensor-memory base
+    return sizeof(R) * size_t(TE) * (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FGR + EG + GM + NBS) +
+           (TC ? size_t(128 + TcShape<P>::B_BYTES + 16) : size_t(0));
 }
 
 // Reference operators: straight-line code with literal coefficients generated
@@ -415,8 +417,15 @@ __device__ __forceinline__ void rhs_part(int part, int comp, int c, const R* us,
 // index of the plan fits (the launcher checks), which saves the 64-bit
 // address arithmetic that is a large part of this kernel's integer work;
 // int64_t otherwise.
-template <int P, typename R, int TE, int NT, int MODE, typename IX = int64_t>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_kernel(const StageParams prm) {
+//
+// TC: tensor-core variant (FP32, p = 2, 3, LSRK4 stages, 64 columns per CTA):
+// the volume curl and the lift (phase 4) run as TF32 split products on the
+// tensor cores (dgm_tc.cuh, TcShape), with tensor-memory row (field, column);
+// phase 5 reads the pre-mass right-hand side from tensor memory.  The other
+// phases are shared with the SIMT kernel.
+template <int P, typename R, int TE, int NT, int MODE, typename IX = int64_t, bool TC = false>
+__global__ void __launch_bounds__(NT, TC ? 1 : ((sizeof(R) == 8 || P <= 3) ? 2 : 1))
+stage_kernel(const StageParams prm) {
     constexpr int N = nmodes(P);
     constexpr int NF = nfmodes(P);
     constexpr int NG = NT / TE;                         // column groups working side by side
@@ -431,6 +440,26 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     R* eg = fg + 4 * FGR * TE;                   // [EG][TE]
     R* gm = eg + EG * TE;                        // [GM][TE] metric A^T A
     int32_t* nbs = reinterpret_cast<int32_t*>(gm + GM * TE);   // [4][TE] neighbour codes
+    static_assert(!TC || (sizeof(R) == 4 && TE == 64 && (MODE == MODE_LSRK || MODE == MODE_RHS) &&
+                          (NT / TE) % 2 == 0 && TcShape<P>::FITS),
+                  "tensor-core variant: FP32, 64 columns, LSRK or right-hand side, even groups");
+    // tensor-core variant: B operand image, mbarrier, tensor-memory base address
+    unsigned char* tc_b = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(nbs + NBS * TE) + 127) & ~uintptr_t(127));
+    uint64_t* tc_bar = reinterpret_cast<uint64_t*>(tc_b + (TC ? TcShape<P>::B_BYTES : 0));
+    uint32_t* tc_base = reinterpret_cast<uint32_t*>(tc_bar + 1);
+    if constexpr (TC) {
+        if (threadIdx.x == 0) tc::mbar_init(tc_bar, 1);
+        if (threadIdx.x < 32) {
+            tc::tmem_alloc(tc_base, TcShape<P>::TCOLS);
+            tc::fence_before();
+        }
+        // the operator image: same for every CTA (an L2 hit after the first ones)
+        const uint4* src = static_cast<const uint4*>(prm.tc_b);
+        uint4* dst = reinterpret_cast<uint4*>(tc_b);
+        for (int i = threadIdx.x; i < TcShape<P>::B_BYTES / 16; i += NT) dst[i] = __ldg(src + i);
+        tc::fence_async_smem();
+    }
 
     const int c = threadIdx.x % TE;
     const int grp = threadIdx.x / TE;
@@ -438,7 +467,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     const int S = prm.S;
     const IX C = K * S;
     const IX col = IX(tile_index(prm.tile_groups)) * TE + c;
-    const bool active = col < C;
+    // only the first K_active elements are updated; the others (halo copies of
+    // another partition's elements) are read as neighbours
+    const bool active = col < IX(prm.K_active) * IX(S);
     const IX e = active ? col / S : 0;
     const int s = active ? int(col - e * S) : 0;
     const R* u = static_cast<const R*>(prm.u);   // may alias u_out (leapfrog)
@@ -597,7 +628,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     // in the element's reference frame, one code path per face (the face of an
     // item is uniform over its warp-sized group)
     {
-        constexpr int CHUNKS = NG >= 12 ? (NG / 4) : 1;      // face-mode chunks per face
+        constexpr int CHUNKS = NG >= 12 ? (NG / 4) : (NG == 8 ? 2 : 1);   // face-mode chunks per face
         R* jp = static_cast<R*>(prm.jumps);
         for (int it = grp; it < 4 * CHUNKS; it += NG) {
             const int f = it / CHUNKS;
@@ -629,7 +660,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
     // copies, so that no conversion runs on the FP64 pipe
     auto coef = [&](double d, float f) { return sizeof(R) == 4 ? R(f) : R(d); };
     if (PREFETCH_RES && grp < 2 * NP5) {
-        const int fb = (grp / NP5) * 3, part = grp % NP5;
+        // tensor-core variant: item (field, part) = (grp % 2, grp / 2), so that a
+        // group reads the tensor-memory rows of its field (lanes of its warps)
+        const int fb = (TC ? grp % 2 : grp / NP5) * 3, part = TC ? grp / 2 : grp % NP5;
         const int lo = part * N / NP5, hi = (part + 1) * N / NP5;
         const bool load = active && coef(prm.a, prm.a_f) != R(0);
         const R* __restrict__ res = static_cast<const R*>(prm.res);
@@ -639,7 +672,105 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             for (int i = 0; i < RP5; ++i)
                 resv[k][i] = (load && (P5_EVEN || lo + i < hi)) ? res[IX((fb + k) * N + lo + i) * C + col] : R(0);
     }
-    for (int it = grp; it < 6 * NPART; it += NG) {
+    // tensor-core variant: per row (field F, column c) stage A_swap = +-s_T times
+    // the other field and the pulled-back fluxes A_g of F's three components in
+    // tensor memory (TF32 hi/lo), then one thread issues the MMAs
+    float tc_dv[3][8];   // phase 5 (tensor-core variant): this item's rows of D
+    if constexpr (TC) {
+        using TS = TcShape<P>;
+        static_assert(NP5 == NG / 2 && (N + NP5 - 1) / NP5 <= 8, "phase-5 items of the tensor-core variant");
+        tc::fence_after();   // the allocation's address, written before the phase-1 barrier
+        const uint32_t tb = *tc_base;
+        const int F = grp % 2, tpart = grp / 2;
+        const uint32_t row = tb + (uint32_t(F * 64 + (c & ~31)) << 16);   // this warp's lanes
+        const R sgn = eg[G_DET * TE + c] < R(0) ? R(-1) : R(1);
+        for (int task = tpart; task < 4; task += NG / 2) {   // uniform over each warp
+            if (task == 0) {
+                const R sF = F == 0 ? sgn : -sgn;
+                const int src = F == 0 ? 3 : 0;
+#pragma unroll
+                for (int k0 = 0; k0 < TS::KC; k0 += 8) {
+                    float hi[8], lo[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int k = k0 + q;
+                        const float v = k < 3 * N ? float(sF * us[(src * N + k) * TE + c]) : 0.0f;
+                        hi[q] = tc::to_tf32(v);
+                        lo[q] = tc::to_tf32(v - hi[q]);
+                    }
+                    tc::tmem_st8(row + TS::T_SWAP_HI + k0, hi);
+                    tc::tmem_st8(row + TS::T_SWAP_LO + k0, lo);
+                }
+            } else {
+                const int j = task - 1, comp = 3 * F + j;
+#pragma unroll
+                for (int k0 = 0; k0 < TS::KL; k0 += 8) {
+                    float hi[8], lo[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int k = k0 + q, f = k / NF, m = k % NF;
+                        // face j + 1 (normal -e_j) has no component j: left out
+                        const float v = (k < 4 * NF && f != j + 1)
+                                            ? float(trO[((f * 6 + comp) * NF + m) * TE + c]) : 0.0f;
+                        hi[q] = tc::to_tf32(v);
+                        lo[q] = tc::to_tf32(v - hi[q]);
+                    }
+                    tc::tmem_st8(row + TS::T_G_HI + j * TS::KL + k0, hi);
+                    tc::tmem_st8(row + TS::T_G_LO + j * TS::KL + k0, lo);
+                }
+            }
+        }
+        tc::tmem_st_wait();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t bimg = tc::smem_addr(tc_b);
+            const uint32_t d = tb + TS::T_D;
+            constexpr uint32_t idc = tc::idesc_tf32(128, TS::NC), idl = tc::idesc_tf32(128, TS::NL);
+            // three TF32 products per k-step, small ones first: lo hi, hi lo, hi hi
+#pragma unroll 1
+            for (int ks = 0; ks < TS::KC / 8; ++ks) {
+                const uint64_t bh = tc::smem_desc(bimg + ks * 256, 128, TS::SBO_CURL);
+                const uint64_t bl = tc::smem_desc(bimg + TS::B_CURL + ks * 256, 128, TS::SBO_CURL);
+                tc::mma_tf32_ts(d, tb + TS::T_SWAP_LO + 8 * ks, bh, idc, ks > 0);
+                tc::mma_tf32_ts(d, tb + TS::T_SWAP_HI + 8 * ks, bl, idc, true);
+                tc::mma_tf32_ts(d, tb + TS::T_SWAP_HI + 8 * ks, bh, idc, true);
+            }
+#pragma unroll 1
+            for (int j = 0; j < 3; ++j)
+#pragma unroll 1
+                for (int ks = 0; ks < TS::KL / 8; ++ks) {
+                    const uint64_t bh = tc::smem_desc(bimg + 2 * TS::B_CURL + ks * 256, 128, TS::SBO_LIFT);
+                    const uint64_t bl = tc::smem_desc(bimg + 2 * TS::B_CURL + TS::B_LIFT + ks * 256, 128,
+                                                      TS::SBO_LIFT);
+                    const uint32_t dj = d + j * N;
+                    tc::mma_tf32_ts(dj, tb + TS::T_G_LO + j * TS::KL + 8 * ks, bh, idl, true);
+                    tc::mma_tf32_ts(dj, tb + TS::T_G_HI + j * TS::KL + 8 * ks, bl, idl, true);
+                    tc::mma_tf32_ts(dj, tb + TS::T_G_HI + j * TS::KL + 8 * ks, bh, idl, true);
+                }
+            tc::mma_commit(tc_bar);
+        }
+        // bounded wait (about a second); on a timeout the status word says so and
+        // the stores of phase 5 are skipped
+        const bool done = __syncthreads_and(tc::mbar_wait(tc_bar, 0, 1u << 22));
+        if (!done && threadIdx.x == 0) atomicOr(prm.status, int32_t(ST_TIMEOUT));
+        tc::fence_after();
+        // this group's phase-5 rows: modes [lo, lo + 8) of the field's 3 components
+        const int lo5 = tpart * N / NP5;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tc::tmem_ld8(row + TS::T_D + k * N + lo5, tc_dv[k]);
+        tc::tmem_ld_wait();
+        if (!done) {   // leave the outputs alone; release tensor memory once the MMAs
+                       // are done (a second bounded wait)
+            tc::mbar_wait(tc_bar, 0, 1u << 22);
+            tc::fence_before();
+            __syncthreads();
+            if (threadIdx.x < 32) tc::tmem_dealloc(tb, TS::TCOLS);
+            return;
+        }
+    }
+    for (int it = grp; it < 6 * NPART && !TC; it += NG) {
         const int comp = it / NPART;
         const int part = it % NPART;
         if (!DO_E && comp < 3) continue;
@@ -669,12 +800,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
         }
     }
     if (MODE == MODE_RAW) return;   // forward quantities for the adjoint only
-    __syncthreads();
+    if (!TC) __syncthreads();
 
     // ---- phase 5: mass-block inverse, PML, update per (field, row part) --------
     for (int it = grp; it < 2 * NP5; it += NG) {
-        const int field = it / NP5;
-        const int part = it % NP5;
+        const int field = TC ? it % 2 : it / NP5;
+        const int part = TC ? it / 2 : it % NP5;
         if (!DO_E && field == 0) continue;
         if (!DO_H && field == 1) continue;
         if (!active) continue;
@@ -757,8 +888,18 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
             R r[3], uv[3], du[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                r[k] = rh[((fb + k) * N + l) * TE + c];
+                if constexpr (TC) r[k] = R(tc_dv[k][i]);
+                else r[k] = rh[((fb + k) * N + l) * TE + c];
                 uv[k] = us[((fb + k) * N + l) * TE + c];
+            }
+            if (TC && field == 0 && prm.src != nullptr) {   // point source (phase 4 of the SIMT path)
+                const double* rec = prm.src + IX(s) * (SRC_HDR + 3 * N);
+                if (rec[0] >= 0.0 && IX(rec[0]) == e) {
+                    const double tt = prm.tdev ? *prm.tdev + prm.t : prm.t;
+                    const R g = R(source_time(tt, rec[1], rec[2], rec[3]));
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) r[k] -= g * R(rec[SRC_HDR + k * N + l]);
+                }
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) du[k] = B[k][0] * r[0] + B[k][1] * r[1] + B[k][2] * r[2];
@@ -796,6 +937,11 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 8 || P <= 3) ? 2 : 1) stage_
                 }
             }
         }
+    }
+    if constexpr (TC) {
+        tc::fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tc::tmem_dealloc(*tc_base, TcShape<P>::TCOLS);
     }
 }
 

@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(NT, 1) stage2_kernel(const StageParams prm) {
     const int S = prm.S;
     const IX C = K * S;
     const IX colA = IX(tile_index(prm.tile_groups)) * 64 + c, colB = colA + 32;
-    const bool actA = colA < C, actB = colB < C;
+    const IX Cact = IX(prm.K_active) * IX(S);     // columns updated (the rest: halo copies)
+    const bool actA = colA < Cact, actB = colB < Cact;
     const IX eA = actA ? colA / S : 0, eB = actB ? colB / S : 0;
     const int sA = actA ? int(colA - eA * S) : 0, sB = actB ? int(colB - eB * S) : 0;
     const float* u = static_cast<const float*>(prm.u);

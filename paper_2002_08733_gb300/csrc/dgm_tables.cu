@@ -3,7 +3,8 @@
 // 1 = 32 x 192, 2 = 16 x 192, and up to p = 3 (where 64 columns of pairs fit
 // in shared memory) 3 = paired kernel with packed FP32x2 arithmetic,
 // 4 = paired kernel with scalar arithmetic; at p >= 4 (one CTA per SM)
-// 3 = 32 x 512.
+// 3 = 32 x 512; at p = 2, 3 also 5 = tensor-core variant (64 columns x 512
+// threads, curl and lift on tcgen05).
 #include "dgm_internal.h"
 #include "dgmax.h"
 
@@ -35,6 +36,7 @@ int launch_p2_f32_lsrk_v1(const StageParams&, void*);
 int launch_p2_f32_lsrk_v2(const StageParams&, void*);
 int launch_p2_f32_lsrk_v3(const StageParams&, void*);
 int launch_p2_f32_lsrk_v4(const StageParams&, void*);
+int launch_p2_f32_lsrk_v5(const StageParams&, void*);
 int launch_p2_f64_rhs(const StageParams&, void*);
 int launch_p2_f64_lsrk(const StageParams&, void*);
 int launch_p2_f64_lfe(const StageParams&, void*);
@@ -51,6 +53,7 @@ int launch_p3_f32_lsrk_v1(const StageParams&, void*);
 int launch_p3_f32_lsrk_v2(const StageParams&, void*);
 int launch_p3_f32_lsrk_v3(const StageParams&, void*);
 int launch_p3_f32_lsrk_v4(const StageParams&, void*);
+int launch_p3_f32_lsrk_v5(const StageParams&, void*);
 int launch_p3_f64_rhs(const StageParams&, void*);
 int launch_p3_f64_lsrk(const StageParams&, void*);
 int launch_p3_f64_lfe(const StageParams&, void*);
@@ -119,6 +122,7 @@ int launch_p2_f32(const StageParams& prm, int mode, void* st) {
             if (prm.variant == 2) return launch_p2_f32_lsrk_v2(prm, st);
             if (prm.variant == 3) return launch_p2_f32_lsrk_v3(prm, st);
             if (prm.variant == 4) return launch_p2_f32_lsrk_v4(prm, st);
+            if (prm.variant == 5) return launch_p2_f32_lsrk_v5(prm, st);
             return launch_p2_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p2_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p2_f32_lfh(prm, st);
@@ -146,6 +150,7 @@ int launch_p3_f32(const StageParams& prm, int mode, void* st) {
             if (prm.variant == 2) return launch_p3_f32_lsrk_v2(prm, st);
             if (prm.variant == 3) return launch_p3_f32_lsrk_v3(prm, st);
             if (prm.variant == 4) return launch_p3_f32_lsrk_v4(prm, st);
+            if (prm.variant == 5) return launch_p3_f32_lsrk_v5(prm, st);
             return launch_p3_f32_lsrk(prm, st);
         case MODE_LF_E: return launch_p3_f32_lfe(prm, st);
         case MODE_LF_H: return launch_p3_f32_lfh(prm, st);
@@ -210,9 +215,9 @@ int launch_p5_f32(const StageParams& prm, int mode, void* st) {
 
 extern const KernelTable kernels_p1_f32 = {launch_p1_f32, 4, launch_p1_f32_adj, 5};
 extern const KernelTable kernels_p1_f64 = {launch_p1_f64, 8, launch_p1_f64_adj, 1};
-extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4, launch_p2_f32_adj, 5};
+extern const KernelTable kernels_p2_f32 = {launch_p2_f32, 4, launch_p2_f32_adj, 6};
 extern const KernelTable kernels_p2_f64 = {launch_p2_f64, 8, launch_p2_f64_adj, 1};
-extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4, launch_p3_f32_adj, 5};
+extern const KernelTable kernels_p3_f32 = {launch_p3_f32, 4, launch_p3_f32_adj, 6};
 extern const KernelTable kernels_p3_f64 = {launch_p3_f64, 8, launch_p3_f64_adj, 1};
 extern const KernelTable kernels_p4_f32 = {launch_p4_f32, 4, launch_p4_f32_adj, 4};
 extern const KernelTable kernels_p4_f64 = {launch_p4_f64, 8, launch_p4_f64_adj, 1};

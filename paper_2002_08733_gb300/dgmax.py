@@ -41,6 +41,12 @@ class Pml(ctypes.Structure):
                 ("order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class HaloSizes(ctypes.Structure):
+    _fields_ = [("n_owned", ctypes.c_int64), ("n_ghost", ctypes.c_int64),
+                ("n_send", ctypes.c_int64), ("n_recv", ctypes.c_int64),
+                ("n_peers", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int64), ("n_pml", ctypes.c_int64), ("N", ctypes.c_int32),
                 ("NF", ctypes.c_int32), ("S", ctypes.c_int32), ("real_size", ctypes.c_int32),
@@ -84,6 +90,14 @@ _SIGS = {
     "dgm_batch_create": [ctypes.POINTER(_P), _P, ctypes.c_int32, _P],
     "dgm_batch_advance": [_P, ctypes.c_int64, _P],
     "dgm_batch_destroy": [_P],
+    "dgm_partition_slabs": [ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int32,
+                            ctypes.c_int32, _P],
+    "dgm_halo_build": [ctypes.c_int64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                       _P, _P, _P],
+    "dgm_set_active": [_P, ctypes.c_int64],
+    "dgm_halo_pack": [_P, _P, _P, ctypes.c_int64, _P],
+    "dgm_halo_unpack": [_P, _P, _P, ctypes.c_int64, _P],
+    "dgm_stage": [_P, ctypes.c_int32, ctypes.c_double],
     "dgm_last_error": [],
     "dgm_plan_destroy": [_P],
 }
@@ -398,6 +412,28 @@ class Solver(Plan):
     def status(self):
         _check(_lib.dgm_status_check(self.handle))
 
+    def set_active(self, n):
+        """Update only the first n elements (the rest are halo copies)."""
+        _check(_lib.dgm_set_active(self.handle, int(n)))
+
+    def stage(self, k, t):
+        """LSRK4 stage k (0..4) of the step starting at time t."""
+        _check(_lib.dgm_stage(self.handle, int(k), float(t)))
+
+    def halo_pack(self, idx_device, out=None, fields=None):
+        """Coefficients of the elements idx_device (int64 device tensor) -> [6N, n, S]."""
+        f = self.fields[self.current()] if fields is None else fields
+        n = int(idx_device.numel())
+        if out is None:
+            out = self.torch.empty((6 * self.N, n, self.S), dtype=self.dtype, device=self.device)
+        _check(_lib.dgm_halo_pack(self.handle, _ptr(f), _ptr(idx_device), n, _ptr(out)))
+        return out
+
+    def halo_unpack(self, idx_device, buf, fields=None):
+        f = self.fields[self.current()] if fields is None else fields
+        _check(_lib.dgm_halo_unpack(self.handle, _ptr(f), _ptr(idx_device), int(idx_device.numel()),
+                                    _ptr(buf)))
+
 
 class Batch:
     """Several bound LSRK4 solvers advanced together by one graph launch per two steps."""
@@ -457,3 +493,175 @@ def receiver_records(solver, eps, mu, n_steps, t0=0.0, u0=None, aux0=None):
 
     return _Records.apply(eps, mu)
 
+
+
+# -- one mesh on several GPUs ------------------------------------------------------------
+
+def partition_slabs(xyz, tets, nparts, axis=2):
+    """Part id per element: slabs of nearly equal size along `axis` (dgm_partition_slabs)."""
+    lib = load_library()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int64)
+    part = np.empty(len(tets), dtype=np.int32)
+    _check(lib.dgm_partition_slabs(len(xyz), xyz.ctypes.data, len(tets), tets.ctypes.data,
+                                   int(axis), int(nparts), part.ctypes.data))
+    return part
+
+
+class Halo:
+    """Part `rank` of an element partition: local numbering (owned elements, then
+    ghosts, each in ascending global id) and, per peer part, the local ids sent
+    to it and received from it (dgm_halo_build).  No GPU needed."""
+
+    def __init__(self, tets, part, nparts, rank):
+        lib = load_library()
+        tets = np.ascontiguousarray(tets, dtype=np.int64)
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        sz = HaloSizes()
+        _check(lib.dgm_halo_build(len(tets), tets.ctypes.data, part.ctypes.data, int(nparts),
+                                  int(rank), ctypes.byref(sz), None, None, None, None, None, None))
+        self.n_owned, self.n_ghost, self.rank = sz.n_owned, sz.n_ghost, rank
+        self.local_to_global = np.empty(sz.n_owned + sz.n_ghost, dtype=np.int64)
+        self.peers = np.empty(max(sz.n_peers, 1), dtype=np.int32)
+        sc = np.empty(max(sz.n_peers, 1), dtype=np.int64)
+        rc = np.empty(max(sz.n_peers, 1), dtype=np.int64)
+        si = np.empty(max(sz.n_send, 1), dtype=np.int64)
+        ri = np.empty(max(sz.n_recv, 1), dtype=np.int64)
+        _check(lib.dgm_halo_build(len(tets), tets.ctypes.data, part.ctypes.data, int(nparts),
+                                  int(rank), ctypes.byref(sz), self.local_to_global.ctypes.data,
+                                  self.peers.ctypes.data, sc.ctypes.data, si.ctypes.data,
+                                  rc.ctypes.data, ri.ctypes.data))
+        self.peers = self.peers[:sz.n_peers]
+        so = np.concatenate([[0], np.cumsum(sc[:sz.n_peers])])
+        ro = np.concatenate([[0], np.cumsum(rc[:sz.n_peers])])
+        self.send = [si[so[q]:so[q + 1]].copy() for q in range(sz.n_peers)]
+        self.recv = [ri[ro[q]:ro[q + 1]].copy() for q in range(sz.n_peers)]
+
+    def exchange(self, pack, unpack, isend, irecv, empty_like_recv):
+        """One halo refresh: receive buffers posted for every peer, this part's
+        send lists packed and sent, then the received coefficients unpacked into
+        the ghosts.  pack(q) -> buffer of peer q's send list, unpack(q, buffer),
+        isend(buffer, peer) / irecv(buffer, peer) -> request with wait(),
+        empty_like_recv(q) -> receive buffer for peer q (e.g. torch.distributed
+        isend/irecv over NCCL or gloo)."""
+        reqs, bufs = [], []
+        for q, peer in enumerate(self.peers):
+            b = empty_like_recv(q)
+            bufs.append(b)
+            reqs.append(irecv(b, int(peer)))
+        for q, peer in enumerate(self.peers):
+            reqs.append(isend(pack(q), int(peer)))
+        for r in reqs:
+            r.wait()
+        for q in range(len(self.peers)):
+            unpack(q, bufs[q])
+
+
+class PartitionedSolver:
+    """This rank's part of a mesh partitioned over ranks (one GPU each): a
+    Solver over its owned elements plus their halo, stepping LSRK4 stage by
+    stage with a halo exchange after each stage.
+
+    exchange: 'dist' (torch.distributed point-to-point, NCCL on GPUs) or None
+    for parts driven together by exchange_local (several parts in one process)."""
+
+    def __init__(self, xyz, tets, eps, mu, p, precision, flux, dt, part, nparts, rank,
+                 pml=None, S=1, device="cuda", exchange="dist"):
+        import torch
+        self.halo = Halo(tets, part, nparts, rank)
+        l2g = self.halo.local_to_global
+        tets = np.asarray(tets)
+        K = len(tets)
+        eps = np.broadcast_to(np.asarray(eps, np.float64), (K,))[l2g]
+        mu = np.broadcast_to(np.asarray(mu, np.float64), (K,))[l2g]
+        self.solver = Solver(xyz, tets[l2g], eps, mu, p, precision, flux, "lsrk4", dt, S=S,
+                             pml=pml, device=device)
+        self._verts = np.asarray(xyz, np.float64)[tets[l2g]]   # local elements' vertices
+        self.solver.set_active(self.halo.n_owned)
+        dev = self.solver.device
+        self.send_idx = [torch.as_tensor(a, device=dev) for a in self.halo.send]
+        self.recv_idx = [torch.as_tensor(a, device=dev) for a in self.halo.recv]
+        self.mode = exchange
+        self.rank = rank
+
+    def _applies(self, pos, tol=1e-12):
+        """Whether this part applies a point source at pos: the lowest global id
+        among the local elements containing it (owned and ghosts) is owned."""
+        V = self._verts
+        A = np.transpose(V[:, 1:] - V[:, :1], (0, 2, 1))          # columns: edges
+        lam = np.linalg.solve(A, (np.asarray(pos, np.float64) - V[:, 0])[:, :, None])[:, :, 0]
+        inside = np.all(lam >= -tol, axis=1) & (lam.sum(axis=1) <= 1 + tol)
+        if not inside.any():
+            return False
+        loc = np.nonzero(inside)[0]
+        return bool(loc[np.argmin(self.halo.local_to_global[loc])] < self.halo.n_owned)
+
+    def set_sources(self, sources):
+        """Point dipoles per column (as Solver.set_sources); each is applied by
+        the part that owns its element."""
+        self.solver.set_sources([rec if rec is not None and self._applies(rec["pos"]) else None
+                                 for rec in sources])
+
+    # state in global element ids
+    def set_state(self, u_global):
+        self.solver.set_state(np.asarray(u_global)[self.halo.local_to_global])
+
+    def owned_state(self):
+        """(global ids of the owned elements, their coefficients (n_owned, S, 6, N))."""
+        u = self.solver.state()
+        n = self.halo.n_owned
+        return self.halo.local_to_global[:n], u[:n]
+
+    def refresh_halo(self):
+        import torch
+        import torch.distributed as dist
+        g = self.solver
+        torch.cuda.synchronize(g.device)   # this stage's outputs are complete
+        self.halo.exchange(
+            pack=lambda q: g.halo_pack(self.send_idx[q]),
+            unpack=lambda q, b: g.halo_unpack(self.recv_idx[q], b),
+            isend=lambda b, peer: dist.isend(b, peer),
+            irecv=lambda b, peer: dist.irecv(b, peer),
+            empty_like_recv=lambda q: torch.empty((6 * g.N, len(self.halo.recv[q]), g.S),
+                                                  dtype=g.dtype, device=g.device))
+
+    def advance(self, n_steps, t0=0.0):
+        t = t0
+        for _ in range(n_steps):
+            for k in range(5):
+                self.solver.stage(k, t)
+                self.refresh_halo()
+            t += self.solver.dt
+
+
+def exchange_local(parts):
+    """Halo refresh of several parts held by one process (one device, or peer
+    copies between devices): each part's send list to a peer is packed and
+    unpacked straight into that peer's ghosts.  No kernel waits on another."""
+    import torch
+    by_rank = {pt.rank: pt for pt in parts}
+    for pt in parts:
+        torch.cuda.synchronize(pt.solver.device)
+    for pt in parts:
+        for q, peer in enumerate(pt.halo.peers):
+            other = by_rank[int(peer)]
+            qq = int(np.nonzero(other.halo.peers == pt.rank)[0][0])
+            buf = pt.solver.halo_pack(pt.send_idx[q])
+            if buf.device != other.solver.device:
+                buf = buf.to(other.solver.device)
+            other.solver.halo_unpack(other.recv_idx[qq], buf)
+    for pt in parts:
+        torch.cuda.synchronize(pt.solver.device)
+
+
+def advance_local(parts, n_steps, t0=0.0):
+    """LSRK4 steps of several parts held by one process, halos refreshed after
+    every stage (exchange_local)."""
+    t = t0
+    dt = parts[0].solver.dt
+    for _ in range(n_steps):
+        for k in range(5):
+            for pt in parts:
+                pt.solver.stage(k, t)
+            exchange_local(parts)
+        t += dt

@@ -84,8 +84,9 @@ def test_batch_member_matches_oracle(D):
 def test_autotuned_variants_match_oracle(D):
     """Every tile-shape variant the autotuner may pick gives the same stage:
     three single-column shapes and, up to p = 3, the paired kernels (two columns
-    per thread, packed FP32x2 and scalar arithmetic).  486 columns leave a
-    ragged last tile for every shape."""
+    per thread, packed FP32x2 and scalar arithmetic) and, at p = 2, 3, the
+    tensor-core variant (curl and lift as TF32 split products on tcgen05).
+    486 columns leave a ragged last tile for every shape."""
     import torch
     xyz, tets = W.kuhn_mesh(3, jitter=0.1, seed=71)
     K, p, S = len(tets), 3, 3
@@ -95,8 +96,8 @@ def test_autotuned_variants_match_oracle(D):
     ref = o.unpack(o.lsrk4(o.pack(u), 0.0, dt, 3))[0]
     g = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", dt, S=S)
     chosen, ms = g.autotune()
-    assert len(ms) == 5 and 0 <= chosen < 5 and np.all(ms > 0)
-    for v in range(5):
+    assert len(ms) == 6 and 0 <= chosen < 6 and np.all(ms > 0)
+    for v in range(6):
         g2 = D.Solver(xyz, tets, 1.0, 1.0, p, "fp32", "upwind", "lsrk4", dt, S=S)
         g2.set_state(u)
         g2.set_variant(v)
@@ -174,10 +175,10 @@ def test_autotuner_variants_high_degree(D, p, prec, nv):
         assert rel_l2(g2.from_device(g2.aux[g2.current()]), ref_aux[g2.pml_elements()]) < tol, v
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
-@pytest.mark.parametrize("v", [3, 4])
+@pytest.mark.parametrize("p,v", [(1, 3), (2, 3), (3, 3), (1, 4), (2, 4), (3, 4), (2, 5), (3, 5)])
 def test_paired_variants_pml_sources_match_oracle(D, p, v):
-    """Paired kernels on a problem where the two columns of a thread differ:
+    """Paired kernels (v = 3, 4) on a problem where the two columns of a thread
+    differ, and the tensor-core variant (v = 5, p = 2, 3) on the same problem:
     PML and non-PML elements, elements with and without a source, jittered
     geometry with element-wise materials, S = 3 columns per element (the last
     without a source)."""

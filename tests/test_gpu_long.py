@@ -78,11 +78,16 @@ def sphere_case():
     return dict(xyz=xyz, tets=tets, eps=eps, p=w.p, u0=u0, dt=dt, per=per, traj=traj)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_jittered_sphere_1000_steps(D, sphere_case, prec, tol):
+@pytest.mark.parametrize("prec,tol,variant", [("fp64", 1e-12, None), ("fp32", 1e-5, None),
+                                              ("fp32", 1e-5, 5)])
+def test_jittered_sphere_1000_steps(D, sphere_case, prec, tol, variant):
+    """variant None: the autotuner's choice; 5: the tensor-core variant (curl and
+    lift as three TF32 products per pair on tcgen05)."""
     c = sphere_case
     g = D.Solver(c["xyz"], c["tets"], c["eps"], 1.0, c["p"], prec, "upwind", "lsrk4", c["dt"])
-    if prec == "fp32":
+    if variant is not None:
+        g.set_variant(variant)
+    elif prec == "fp32":
         g.autotune()
     g.set_state(c["u0"])
     got = []
