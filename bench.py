@@ -227,26 +227,31 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     return out
 
 
-def run_pml(precision, steps, warmup, n=40):
+def run_pml(precision, steps, warmup, n=40, integrator="lsrk4"):
     """Dipole-in-PML workload: [-1,1]^3 on an n^3 Kuhn grid (384,000 tets at n=40),
     p=4, PML 0.25 thick with quadratic profile and sigma_max=40, z-directed
-    dipole, upwind flux, LSRK4, starting from rest.  Returns timing and the
-    algorithmic bytes of one step (fields plus PML auxiliaries)."""
+    dipole, starting from rest; upwind flux with LSRK4 or, with
+    integrator="leapfrog", the central flux with staggered leapfrog and the
+    PML terms by the trapezoid rule (two launches per step).  Returns timing
+    and the algorithmic bytes of one step (fields plus PML auxiliaries)."""
     import torch
     from paper_2002_08733_gb300 import dgmax as D
     w = W.dipole_pml(n=n)
     xyz, tets = w.mesh()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
-    g = D.Solver(xyz, tets, 1.0, 1.0, w.p, precision, w.flux, w.integrator, w.dt, device=dev,
+    flux = w.flux if integrator == "lsrk4" else "central"
+    g = D.Solver(xyz, tets, 1.0, 1.0, w.p, precision, flux, integrator, w.dt, device=dev,
                  stream=stream, pml=w.pml)
     g.set_sources(w.extra["sources"])
     tuned = None
-    if precision == "fp32":   # the plan's own tile-shape choice (state untouched)
+    if precision == "fp32" and integrator == "lsrk4":   # tile shape (state untouched)
         v, ms_v = g.autotune()
         tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms_v],
                  "tile_groups": g.tile_groups()}
     t = 0.0
+    if integrator == "leapfrog":
+        g.leapfrog_start(0.0)
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             g.advance(1, t)
@@ -268,7 +273,10 @@ def run_pml(precision, steps, warmup, n=40):
     field = 6 * g.N * g.K * rs
     aux = 6 * g.N * g.npml * rs
     geo = g.K * (16 * rs + 4 * 4 + 4)
-    step_bytes = (3 * field + 3 * aux + geo) + 4 * (4 * field + 4 * aux + geo)
+    if integrator == "lsrk4":
+        step_bytes = (3 * field + 3 * aux + geo) + 4 * (4 * field + 4 * aux + geo)
+    else:   # two launches: read both fields, write one; read both auxiliaries, write one
+        step_bytes = 2 * (field + field // 2 + aux + aux // 2 + geo)
     return dict(value=dofs * steps / (ms * 1e-3), ms_per_step=ms / steps, steps=steps, K=g.K,
                 N=g.N, n_pml=g.npml, bytes_per_step=step_bytes,
                 hbm_frac=step_bytes / (ms / steps * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0),
@@ -744,6 +752,12 @@ def main():
                                       "PML 0.25 sigma_max=40, z dipole, upwind, LSRK4, from rest",
                           "fp32": p32, "fp64": p64, "fp32_over_fp64": p32["value"] / p64["value"],
                           "fp32_vs_fp64_rel_l2_after_%d_steps" % (args.pml_steps + 3): err}
+        lf32 = run_pml("fp32", args.pml_steps, 3, integrator="leapfrog")
+        lf32.pop("_final")
+        line["p4_pml_leapfrog"] = {
+            "workload": "the same dipole-in-PML mesh and source, central flux, staggered "
+                        "leapfrog with the PML terms by the trapezoid rule (Sec. V), same dt",
+            "fp32": lf32, "lsrk4_fp32_ms_per_step": p32["ms_per_step"]}
     if not args.no_batched and world == 1:
         line["batched"] = dict(workload="64 dipoles on a 24^3 PML mesh (p=3, S=64) + 16 PEC "
                                         "cavities n 6..28, p 2..5; FP32; one graph launch per "

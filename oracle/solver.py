@@ -165,6 +165,95 @@ class Solver:
                 callback(n + 1, t, x)
         return x
 
+    def leapfrog_pml(self, x, t0, dt, steps, callback=None):
+        """Staggered leapfrog with the PML's dissipative terms taken by the
+        trapezoid rule (Sec. V: leap-frog, dissipative terms by the trapezoid
+        rule, explicit because every such term is element-local).
+
+        Unknowns: e at integer steps, h at half steps; the auxiliaries p (of the
+        E equation) at half steps and q (of the H equation) at integer steps, so
+        that every equation is centred.  With the element mass M1, the PML
+        matrices M_eta, M_Sigma, M_xi of Sec. IV and the curl/flux blocks K_EH,
+        K_HE of the central flux, one step from (e^n, h^{n+1/2}, p^{n+1/2}, q^n):
+
+          (M1 + dt/2 M_Sigma) q^{n+1}   = (M1 - dt/2 M_Sigma) q^n + dt mu M_xi h^{n+1/2}
+          eps (M1 + dt/2 M_eta) e^{n+1} = eps (M1 - dt/2 M_eta) e^n
+                                          + dt (K_EH h^{n+1/2} - M1 p^{n+1/2} - (j, phi)(t + dt/2))
+          (M1 + dt/2 M_Sigma) p^{n+3/2} = (M1 - dt/2 M_Sigma) p^{n+1/2} + dt eps M_xi e^{n+1}
+          mu (M1 + dt/2 M_eta) h^{n+3/2} = mu (M1 - dt/2 M_eta) h^{n+1/2}
+                                          + dt (K_HE e^{n+1} - M1 q^{n+1})
+
+        Start (h, q and p given at t0): h and p advance half a step with the
+        same updates over dt/2 from e^0, q^0.  On return e is at t0 + steps dt
+        and h, p half a step later.  Without a PML (or with sigma = 0) this is
+        the plain staggered leapfrog."""
+        a = self.asm
+        K, n3 = a.K, a.n3
+        assert a.flux == "central" and a.R == K
+        nE = K * n3
+        Keh = a.Kmat[:nE, nE:2 * nE]
+        Khe = a.Kmat[nE:2 * nE, :nE]
+        M1 = a.M1
+        eps = a.eps[:, None, None]
+        mu = a.mu[:, None, None]
+        if a.has_pml:
+            Eta, Sig, Xi = a.pml_blocks["eta"], a.pml_blocks["sig"], a.pml_blocks["xi"]
+            # auxiliaries exist only in elements with a damping (elsewhere they
+            # are not coupled, as in the assembled operator)
+            M1aux = M1 * np.any(a.sigma[a.rows] != 0.0, axis=1)[:, None, None]
+        else:
+            Eta = Sig = Xi = np.zeros_like(M1)
+            M1aux = np.zeros_like(M1)
+        blk = lambda v, b: v[b * nE:(b + 1) * nE].reshape(K, n3, -1)
+        mv = lambda Mats, v: np.matmul(Mats, v)
+
+        def field_update(v, mat, rhs_vec, h):
+            """mat (M1 + h/2 M_eta) v_new = mat (M1 - h/2 M_eta) v + h rhs."""
+            A = mat * (M1 + 0.5 * h * Eta)
+            B = mat * (M1 - 0.5 * h * Eta)
+            return np.linalg.solve(A, mv(B, v) + h * rhs_vec)
+
+        def aux_update(v, drive, h):
+            """(M1 + h/2 M_Sigma) v_new = (M1 - h/2 M_Sigma) v + h drive."""
+            return np.linalg.solve(M1 + 0.5 * h * Sig, mv(M1 - 0.5 * h * Sig, v) + h * drive)
+
+        x = x.copy()
+        S = x.shape[1]
+        e, hf = blk(x, 0).copy(), blk(x, 1).copy()
+        p = blk(x, 2).copy() if a.nblk == 4 else np.zeros_like(e)
+        q = blk(x, 3).copy() if a.nblk == 4 else np.zeros_like(e)
+
+        def src(t):
+            if not self.src:
+                return 0.0
+            return self.source_vector(t)[:nE].reshape(K, n3, S)
+
+        def h_step(e_, h_, q_, h):
+            curl = (Khe @ e_.reshape(nE, S)).reshape(K, n3, S)
+            return field_update(h_, mu, curl - mv(M1aux, q_), h)
+
+        def e_step(e_, h_, p_, t, h):
+            curl = (Keh @ h_.reshape(nE, S)).reshape(K, n3, S)
+            return field_update(e_, eps, curl - mv(M1aux, p_) + src(t), h)
+
+        hf = h_step(e, hf, q, 0.5 * dt)
+        p = aux_update(p, eps * mv(Xi, e), 0.5 * dt)
+        t = t0
+        for n in range(steps):
+            q = aux_update(q, mu * mv(Xi, hf), dt)
+            e = e_step(e, hf, p, t + 0.5 * dt, dt)
+            p = aux_update(p, eps * mv(Xi, e), dt)
+            hf = h_step(e, hf, q, dt)
+            t += dt
+            if callback is not None:
+                out = np.concatenate([e.reshape(nE, S), hf.reshape(nE, S)] +
+                                     ([p.reshape(nE, S), q.reshape(nE, S)] if a.nblk == 4 else []))
+                callback(n + 1, t, out)
+        parts = [e.reshape(nE, S), hf.reshape(nE, S)]
+        if a.nblk == 4:
+            parts += [p.reshape(nE, S), q.reshape(nE, S)]
+        return np.concatenate(parts)
+
     # -- projection and sampling --------------------------------------------------
     def project(self, fn, field):
         """L2 projection of a vector function fn(r [n,3]) -> [n,3] onto field 'E' or 'H'.

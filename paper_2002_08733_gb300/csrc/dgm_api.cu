@@ -101,7 +101,7 @@ static void build_tc_image_p(const std::vector<double>& S, const std::vector<dou
                 for (int l = 0; l < N; ++l) {
                     double v = S[(size_t(a) * N + l) * N + m];
                     if (!(std::fabs(v) > 1e-13 * smax)) continue;
-                    split(0, TS::B_CURL, j * N + l, i * N + m, TS::KC, eps * v);
+                    split(0, TS::B_CURL, j * TS::NL + l, i * N + m, TS::KC, eps * v);
                 }
         }
     for (int f = 0; f < 4; ++f)
@@ -259,8 +259,8 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
     if (opt->flux != DGM_CENTRAL && opt->flux != DGM_UPWIND) return fail(DGM_EINVAL, "unknown flux");
     if (opt->integrator != DGM_LEAPFROG && opt->integrator != DGM_LSRK4)
         return fail(DGM_EINVAL, "unknown integrator");
-    if (opt->integrator == DGM_LEAPFROG && (opt->flux != DGM_CENTRAL || pml))
-        return fail(DGM_EUNSUP, "leapfrog needs the central flux and no PML");
+    if (opt->integrator == DGM_LEAPFROG && opt->flux != DGM_CENTRAL)
+        return fail(DGM_EUNSUP, "leapfrog needs the central flux");
     const KernelTable* kt = kernel_table(opt->p, opt->precision);
     if (!kt) return fail(DGM_EUNSUP, "unsupported polynomial degree / precision");
     if (pml) {
@@ -626,6 +626,8 @@ int dgm_leapfrog_start(dgm_plan* P, double t0) {
     stage_params(P, prm);
     prm.u = P->fields[P->cur];
     prm.u_out = P->fields[P->cur];
+    prm.aux = P->aux[P->cur];       // PML auxiliaries, updated in place
+    prm.aux_out = P->aux[P->cur];
     prm.dt = 0.5 * P->opt.dt;
     prm.t = t0;
     int rc = P->kt->launch_stage(prm, MODE_LF_H, P->stream);
@@ -658,6 +660,8 @@ int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
         } else {
             prm.u = P->fields[P->cur];
             prm.u_out = P->fields[P->cur];
+            prm.aux = P->aux[P->cur];   // PML auxiliaries, updated in place
+            prm.aux_out = P->aux[P->cur];
             prm.t = t + 0.5 * dt;
             int rc = P->kt->launch_stage(prm, MODE_LF_E, P->stream);
             if (rc) return fail(rc, "stage kernel launch failed");

@@ -26,23 +26,22 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 // index i N + m for component i, mode m), B_curl[(i, m)][(j, l)] =
 // eps_jai S_a[l][m] (the reference curl of Eq. (matrix_free_curl)), A_g,j the
 // pulled-back face fluxes of component j (K = 4 NF, index f NF + m) and
-// B_lift[(f, m)][l] = R_f[m][l] (the lift of Eqs. (uwc)/(cwc)).  Component j's
-// lift lands in D columns [j N, j N + NL), which overlap the next component's
-// first columns only where B_lift has zero padding.
+// B_lift[(f, m)][l] = R_f[m][l] (the lift of Eqs. (uwc)/(cwc)).  Component j
+// of D occupies columns [j NL, j NL + N) (NL = N rounded up to 16), so every
+// MMA output and every tensor-memory load starts on a multiple of 16 columns.
 template <int P>
 struct TcShape {
     static constexpr int N = nmodes(P), NF = nfmodes(P);
     static constexpr int KC = round_up(3 * N, 8);     // curl: K (TF32 steps of 8)
-    static constexpr int NC = round_up(3 * N, 16);    // curl: N (multiple of 16 at M = 128)
-    static constexpr int KL = round_up(4 * NF, 8);    // lift: K per component
     static constexpr int NL = round_up(N, 16);        // lift: N per component
-    static constexpr int ND = NC > 2 * N + NL ? NC : 2 * N + NL;   // D columns touched
+    static constexpr int NC = 3 * NL;                 // curl: N (all three components)
+    static constexpr int KL = round_up(4 * NF, 8);    // lift: K per component
     // tensor-memory columns: A_swap hi/lo, A_g hi/lo (3 components each), D
     static constexpr int T_SWAP_HI = 0, T_SWAP_LO = KC;
     static constexpr int T_G_HI = 2 * KC, T_G_LO = 2 * KC + 3 * KL;
     static constexpr int T_D = round_up(2 * KC + 6 * KL, 32);
     static constexpr int TCOLS = 512;
-    static constexpr bool FITS = T_D + ND <= TCOLS;   // tensor-memory budget
+    static constexpr bool FITS = T_D + NC <= TCOLS;   // tensor-memory budget
     // B image (bytes, K-major core matrices): curl hi, curl lo, lift hi, lift lo
     static constexpr int B_CURL = NC * KC * 4, B_LIFT = NL * KL * 4;
     static constexpr int B_BYTES = 2 * B_CURL + 2 * B_LIFT;

@@ -93,9 +93,10 @@ constexpr int GM = 6;    // metric A^T A per column: entries 00, 01, 02, 11, 12,
 
 template <int P, typename R, int TE, bool TC = false>
 __host__ __device__ constexpr size_t stage_smem_bytes() {
-    // tensor-core variant: + B operand image, an mbarrier and the tensor-memory base
+    // tensor-core variant: + an mbarrier and the tensor-memory base (the operator
+    // image lives in the neighbour-trace array, dead after phase 3)
     return sizeof(R) * size_t(TE) * (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FGR + EG + GM + NBS) +
-           (TC ? size_t(128 + TcShape<P>::B_BYTES + 16) : size_t(0));
+           (TC ? size_t(32) : size_t(0));
 }
 
 // Reference operators: straight-line code with literal coefficients generated
@@ -443,22 +444,19 @@ stage_kernel(const StageParams prm) {
     static_assert(!TC || (sizeof(R) == 4 && TE == 64 && (MODE == MODE_LSRK || MODE == MODE_RHS) &&
                           (NT / TE) % 2 == 0 && TcShape<P>::FITS),
                   "tensor-core variant: FP32, 64 columns, LSRK or right-hand side, even groups");
-    // tensor-core variant: B operand image, mbarrier, tensor-memory base address
-    unsigned char* tc_b = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(nbs + NBS * TE) + 127) & ~uintptr_t(127));
-    uint64_t* tc_bar = reinterpret_cast<uint64_t*>(tc_b + (TC ? TcShape<P>::B_BYTES : 0));
+    // tensor-core variant: mbarrier and tensor-memory base address after the
+    // tables; the operator image goes into the neighbour-trace array in phase 4
+    uint64_t* tc_bar = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(nbs + NBS * TE) + 7) & ~uintptr_t(7));
     uint32_t* tc_base = reinterpret_cast<uint32_t*>(tc_bar + 1);
     if constexpr (TC) {
+        static_assert(TcShape<P>::B_BYTES <= int(sizeof(R)) * 24 * nfmodes(P) * TE,
+                      "operator image fits in the neighbour-trace array");
         if (threadIdx.x == 0) tc::mbar_init(tc_bar, 1);
         if (threadIdx.x < 32) {
             tc::tmem_alloc(tc_base, TcShape<P>::TCOLS);
             tc::fence_before();
         }
-        // the operator image: same for every CTA (an L2 hit after the first ones)
-        const uint4* src = static_cast<const uint4*>(prm.tc_b);
-        uint4* dst = reinterpret_cast<uint4*>(tc_b);
-        for (int i = threadIdx.x; i < TcShape<P>::B_BYTES / 16; i += NT) dst[i] = __ldg(src + i);
-        tc::fence_async_smem();
     }
 
     const int c = threadIdx.x % TE;
@@ -660,9 +658,7 @@ stage_kernel(const StageParams prm) {
     // copies, so that no conversion runs on the FP64 pipe
     auto coef = [&](double d, float f) { return sizeof(R) == 4 ? R(f) : R(d); };
     if (PREFETCH_RES && grp < 2 * NP5) {
-        // tensor-core variant: item (field, part) = (grp % 2, grp / 2), so that a
-        // group reads the tensor-memory rows of its field (lanes of its warps)
-        const int fb = (TC ? grp % 2 : grp / NP5) * 3, part = TC ? grp / 2 : grp % NP5;
+        const int fb = (grp / NP5) * 3, part = grp % NP5;
         const int lo = part * N / NP5, hi = (part + 1) * N / NP5;
         const bool load = active && coef(prm.a, prm.a_f) != R(0);
         const R* __restrict__ res = static_cast<const R*>(prm.res);
@@ -675,12 +671,19 @@ stage_kernel(const StageParams prm) {
     // tensor-core variant: per row (field F, column c) stage A_swap = +-s_T times
     // the other field and the pulled-back fluxes A_g of F's three components in
     // tensor memory (TF32 hi/lo), then one thread issues the MMAs
-    float tc_dv[3][8];   // phase 5 (tensor-core variant): this item's rows of D
     if constexpr (TC) {
         using TS = TcShape<P>;
-        static_assert(NP5 == NG / 2 && (N + NP5 - 1) / NP5 <= 8, "phase-5 items of the tensor-core variant");
         tc::fence_after();   // the allocation's address, written before the phase-1 barrier
         const uint32_t tb = *tc_base;
+        // the operator image, the same for every CTA (an L2 hit after the first
+        // ones), into the neighbour-trace array (dead since phase 3)
+        unsigned char* tc_b = reinterpret_cast<unsigned char*>(trN);
+        {
+            const uint4* src = static_cast<const uint4*>(prm.tc_b);
+            uint4* dst = reinterpret_cast<uint4*>(tc_b);
+            for (int i = threadIdx.x; i < TcShape<P>::B_BYTES / 16; i += NT) dst[i] = __ldg(src + i);
+            tc::fence_async_smem();
+        }
         const int F = grp % 2, tpart = grp / 2;
         const uint32_t row = tb + (uint32_t(F * 64 + (c & ~31)) << 16);   // this warp's lanes
         const R sgn = eg[G_DET * TE + c] < R(0) ? R(-1) : R(1);
@@ -744,30 +747,54 @@ stage_kernel(const StageParams prm) {
                     const uint64_t bh = tc::smem_desc(bimg + 2 * TS::B_CURL + ks * 256, 128, TS::SBO_LIFT);
                     const uint64_t bl = tc::smem_desc(bimg + 2 * TS::B_CURL + TS::B_LIFT + ks * 256, 128,
                                                       TS::SBO_LIFT);
-                    const uint32_t dj = d + j * N;
+                    const uint32_t dj = d + j * TS::NL;
                     tc::mma_tf32_ts(dj, tb + TS::T_G_LO + j * TS::KL + 8 * ks, bh, idl, true);
                     tc::mma_tf32_ts(dj, tb + TS::T_G_HI + j * TS::KL + 8 * ks, bl, idl, true);
                     tc::mma_tf32_ts(dj, tb + TS::T_G_HI + j * TS::KL + 8 * ks, bh, idl, true);
                 }
             tc::mma_commit(tc_bar);
         }
-        // bounded wait (about a second); on a timeout the status word says so and
-        // the stores of phase 5 are skipped
-        const bool done = __syncthreads_and(tc::mbar_wait(tc_bar, 0, 1u << 22));
+        // bounded wait (half a second of wall time, none once another CTA of the
+        // launch has given up); on a timeout the status word says so and the
+        // stores of phase 5 are skipped
+        const bool failed_before = (*reinterpret_cast<volatile int32_t*>(prm.status) & ST_TIMEOUT) != 0;
+        const bool done = __syncthreads_and(!failed_before && tc::mbar_wait(tc_bar, 0, 500000000ull));
         if (!done && threadIdx.x == 0) atomicOr(prm.status, int32_t(ST_TIMEOUT));
         tc::fence_after();
-        // this group's phase-5 rows: modes [lo, lo + 8) of the field's 3 components
-        const int lo5 = tpart * N / NP5;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) tc::tmem_ld8(row + TS::T_D + k * N + lo5, tc_dv[k]);
-        tc::tmem_ld_wait();
         if (!done) {   // leave the outputs alone; release tensor memory once the MMAs
                        // are done (a second bounded wait)
-            tc::mbar_wait(tc_bar, 0, 1u << 22);
+            tc::mbar_wait(tc_bar, 0, 500000000ull);
             tc::fence_before();
             __syncthreads();
             if (threadIdx.x < 32) tc::tmem_dealloc(tb, TS::TCOLS);
             return;
+        }
+        // D rows (aligned 16-column chunks, shared by the field's groups) into the
+        // right-hand-side array of phase 5, with the point source of the E rows
+        for (int ch = tpart; ch < TS::NC / 16; ch += NG / 2) {
+            float v[16];
+            tc::tmem_ld16(row + TS::T_D + 16 * ch, v);
+            tc::tmem_ld_wait();
+            R gsrc = R(0);
+            const double* rec = nullptr;
+            if (F == 0 && prm.src != nullptr && active) {
+                rec = prm.src + IX(s) * (SRC_HDR + 3 * N);
+                if (rec[0] >= 0.0 && IX(rec[0]) == e) {
+                    const double tt = prm.tdev ? *prm.tdev + prm.t : prm.t;
+                    gsrc = R(source_time(tt, rec[1], rec[2], rec[3]));
+                } else {
+                    rec = nullptr;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int col16 = 16 * ch + q, j = col16 / TS::NL, l = col16 % TS::NL;
+                if (l < N) {
+                    R val = R(v[q]);
+                    if (rec != nullptr) val -= gsrc * R(rec[SRC_HDR + j * N + l]);
+                    rh[((3 * F + j) * N + l) * TE + c] = val;
+                }
+            }
         }
     }
     for (int it = grp; it < 6 * NPART && !TC; it += NG) {
@@ -800,12 +827,12 @@ stage_kernel(const StageParams prm) {
         }
     }
     if (MODE == MODE_RAW) return;   // forward quantities for the adjoint only
-    if (!TC) __syncthreads();
+    __syncthreads();
 
     // ---- phase 5: mass-block inverse, PML, update per (field, row part) --------
     for (int it = grp; it < 2 * NP5; it += NG) {
-        const int field = TC ? it % 2 : it / NP5;
-        const int part = TC ? it / 2 : it % NP5;
+        const int field = it / NP5;
+        const int part = it % NP5;
         if (!DO_E && field == 0) continue;
         if (!DO_H && field == 1) continue;
         if (!active) continue;
@@ -827,12 +854,12 @@ stage_kernel(const StageParams prm) {
         int32_t pi = -1;
         if (prm.pml != nullptr) pi = prm.pml[e];
         R ETA[3][3], SIG[3][3], XI[3][3];
+        constexpr bool LF = (MODE == MODE_LF_E || MODE == MODE_LF_H);
+        R ait[9], AT[3][3], sg3[3], et3[3], xi3[3];   // PML: A^-T, A^T, sigma, eta, xi
         if (pi >= 0) {
-            R ait[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) ait[k] = eg[(G_AIT + k) * TE + c];
             // A^T = adj(A^-T) det A
-            R AT[3][3];
             AT[0][0] = ait[4] * ait[8] - ait[5] * ait[7];
             AT[0][1] = ait[2] * ait[7] - ait[1] * ait[8];
             AT[0][2] = ait[1] * ait[5] - ait[2] * ait[4];
@@ -848,11 +875,11 @@ stage_kernel(const StageParams prm) {
                 for (int b = 0; b < 3; ++b) AT[a][b] *= det;
             const R sx = eg[(G_SIG + 0) * TE + c], sy = eg[(G_SIG + 1) * TE + c],
                     sz = eg[(G_SIG + 2) * TE + c];
-            const R sg3[3] = {sx, sy, sz};
-            const R et3[3] = {sy + sz - sx, sz + sx - sy, sx + sy - sz};
-            const R xi3[3] = {(sx - sy) * (sx - sz), (sy - sz) * (sy - sx), (sz - sx) * (sz - sy)};
+            sg3[0] = sx; sg3[1] = sy; sg3[2] = sz;
+            et3[0] = sy + sz - sx; et3[1] = sz + sx - sy; et3[2] = sx + sy - sz;
+            xi3[0] = (sx - sy) * (sx - sz); xi3[1] = (sy - sz) * (sy - sx); xi3[2] = (sz - sx) * (sz - sy);
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
+            for (int j = 0; j < 3 && !LF; ++j)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     ETA[j][k] = R(0);
@@ -888,21 +915,53 @@ stage_kernel(const StageParams prm) {
             R r[3], uv[3], du[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                if constexpr (TC) r[k] = R(tc_dv[k][i]);
-                else r[k] = rh[((fb + k) * N + l) * TE + c];
+                r[k] = rh[((fb + k) * N + l) * TE + c];
                 uv[k] = us[((fb + k) * N + l) * TE + c];
-            }
-            if (TC && field == 0 && prm.src != nullptr) {   // point source (phase 4 of the SIMT path)
-                const double* rec = prm.src + IX(s) * (SRC_HDR + 3 * N);
-                if (rec[0] >= 0.0 && IX(rec[0]) == e) {
-                    const double tt = prm.tdev ? *prm.tdev + prm.t : prm.t;
-                    const R g = R(source_time(tt, rec[1], rec[2], rec[3]));
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) r[k] -= g * R(rec[SRC_HDR + k * N + l]);
-                }
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) du[k] = B[k][0] * r[0] + B[k][1] * r[1] + B[k][2] * r[2];
+            if (LF && pi >= 0) {
+                // Leapfrog with the PML terms by the trapezoid rule (Sec. V), per
+                // Cartesian component in the physical frame X = A^-T x (the 3x3
+                // mass blocks become diagonal there):
+                //   X_new = ((1 - dt eta/2) X + dt (A^-T du - A^-T aux / mat)) / (1 + dt eta/2)
+                // with du the mass-inverted curl/flux terms and aux this field's
+                // auxiliary (p for E, q for H); then the other field's auxiliary
+                //   Z_new = gamma Z + dt beta mat' xi Y,  beta = 1/(1 + dt sigma/2),
+                //   gamma = (1 - dt sigma/2) beta,  Y = A^-T (other field), mat' its
+                // material; covariant coefficients are A^T times physical ones.
+                const int ob = 3 - fb;                         // the other field
+                const R omat = field == 0 ? eg[G_MU * TE + c] : eg[G_EPS * TE + c];
+                const IX abo = IX(ob * N + lo) * C2 + acol;    // (ob, lo) in the auxiliaries
+                R* auxl = static_cast<R*>(prm.aux_out);        // in place: aux_out == aux
+                R av[3], ov[3], oa[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    av[k] = auxl[ab + IX(k * N + i) * C2];
+                    ov[k] = us[((ob + k) * N + l) * TE + c];
+                    oa[k] = auxl[abo + IX(k * N + i) * C2];
+                }
+                R Xn[3], Zn[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const R x = ait[3 * a] * uv[0] + ait[3 * a + 1] * uv[1] + ait[3 * a + 2] * uv[2];
+                    const R y = ait[3 * a] * du[0] + ait[3 * a + 1] * du[1] + ait[3 * a + 2] * du[2];
+                    const R z = ait[3 * a] * av[0] + ait[3 * a + 1] * av[1] + ait[3 * a + 2] * av[2];
+                    const R hd = R(0.5) * dt * et3[a];
+                    Xn[a] = ((R(1) - hd) * x + dt * (y - z * imat)) / (R(1) + hd);
+                    const R yo = ait[3 * a] * ov[0] + ait[3 * a + 1] * ov[1] + ait[3 * a + 2] * ov[2];
+                    const R zo = ait[3 * a] * oa[0] + ait[3 * a + 1] * oa[1] + ait[3 * a + 2] * oa[2];
+                    const R beta = R(1) / (R(1) + R(0.5) * dt * sg3[a]);
+                    const R gamma = (R(1) - R(0.5) * dt * sg3[a]) * beta;
+                    Zn[a] = gamma * zo + dt * beta * omat * xi3[a] * yo;
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    uo[gb + IX(k * N + i) * C] = AT[k][0] * Xn[0] + AT[k][1] * Xn[1] + AT[k][2] * Xn[2];
+                    auxl[abo + IX(k * N + i) * C2] = AT[k][0] * Zn[0] + AT[k][1] * Zn[1] + AT[k][2] * Zn[2];
+                }
+                continue;
+            }
             if (pi >= 0) {
                 R av[3];
 #pragma unroll
