@@ -18,10 +18,10 @@ from __future__ import annotations
 
 import os
 
-# the oracle's per-element dense products stay single-threaded; its sparse
-# operator product runs on PyTorch's CPU threads, one per host core (reported
-# as cores)
+# the oracle runs on one host core (reported as cores)
+os.environ.setdefault("OMP_NUM_THREADS", "1")
 os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
 
 import argparse
 import json
@@ -501,17 +501,12 @@ def run_e2e(g, steps, t0, world=1):
 
 
 SPHERE_REPLICA_N = 3
+# the replica's layer starts at |x| = 0.6 (0.4 thick) so that its centroids (at
+# 0.25, 0.5, 0.75 of a unit cube) are damped; the full workload's 0.25-thick
+# layer at 0.75 would damp none of them
 DIPOLE_REPLICA = dict(n=2, src=(0.13, -0.21, 0.08),
-                      pml=dict(lo=(-0.75,) * 3, hi=(0.75,) * 3, thickness=0.25,
+                      pml=dict(lo=(-0.6,) * 3, hi=(0.6,) * 3, thickness=0.4,
                                sigma_max=40.0, order=2))
-
-
-def host_threads():
-    """One PyTorch CPU thread per core this process may run on."""
-    import torch
-    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    torch.set_num_threads(max(1, int(n or 1)))
-    return torch.get_num_threads()
 
 
 def cpu_reference():
@@ -520,8 +515,8 @@ def cpu_reference():
 
     * jittered sphere (p = 3, eps = 4 sphere, upwind, LSRK4, Gaussian pulse) on
       a 3^3 jittered grid (162 elements), 1000 steps -- timed: the CPU baseline;
-    * dipole in the PML (p = 4, PML 0.25 thick, sigma_max 40, z dipole from rest)
-      on a 2^3 grid of [-1,1]^3 (48 elements), 2000 steps.
+    * dipole in a PML (p = 4, quadratic layer with sigma_max 40, z dipole from
+      rest) on a 2^3 grid of [-1,1]^3 (48 elements), 2000 steps.
 
     Returns the baseline record and, for each replica, what the GPU runs need
     to be compared with the oracle (initial state from the oracle's own
@@ -530,7 +525,6 @@ def cpu_reference():
     from oracle.assemble import Assembly, pml_sigma
     from oracle.mesh import Mesh
     from oracle.solver import Solver as OSolver
-    host_threads()
     full = W.jittered_sphere()
     w = W.jittered_sphere(n=SPHERE_REPLICA_N)
     xyz, tets, eps = build_problem(w)
@@ -544,14 +538,13 @@ def cpu_reference():
     x = o.lsrk4(o.pack(u0), 0.0, full.dt, full.steps)
     el = time.perf_counter() - start
     dofs = 6 * o.asm.N * o.asm.K
-    base = dict(value=dofs * full.steps / el, unit=UNIT, cores=torch.get_num_threads(),
+    base = dict(value=dofs * full.steps / el, unit=UNIT, cores=1,
                 kind="oracle", seconds=el,
                 sample="jittered-sphere workload (p=3, upwind, LSRK4, eps=4 sphere, Gaussian "
                        "pulse) on a %d^3 jittered Kuhn grid (%d elements), %d LSRK4 steps of "
                        "dt=%.4g as in the full workload; assembly and projection excluded; "
-                       "the sparse operator product on %d PyTorch CPU threads"
-                       % (SPHERE_REPLICA_N, o.asm.K, full.steps, full.dt,
-                          torch.get_num_threads()))
+                       "one host core (scipy sparse products)"
+                       % (SPHERE_REPLICA_N, o.asm.K, full.steps, full.dt))
     sphere = dict(xyz=xyz, tets=tets, eps=eps, p=w.p, dt=full.dt, steps=full.steps, u0=u0,
                   ref=o.unpack(x)[0],
                   workload="jittered sphere on a %d^3 replica grid (%d elements), p=3, %d "
@@ -650,8 +643,6 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        import torch
-        host_threads()
         steps, warm = args.steps, args.warmup
         from oracle.assemble import Assembly
         from oracle.mesh import Mesh
@@ -671,8 +662,7 @@ def main():
         v = dofs * steps / el
         sample = ("each step: one LSRK4 step (dt of the 32^3 workload) of the oracle on the "
                   "jittered-sphere workload at %d^3 (%d elements, p=3), assembly excluded; "
-                  "sparse operator product on %d PyTorch CPU threads"
-                  % (n_ref, o.asm.K, torch.get_num_threads()))
+                  "one host core (scipy sparse products)" % (n_ref, o.asm.K))
         ref_config = dict(config)
         ref_config.update(
             workload="jittered_sphere sample: %d^3 Kuhn grid of [0,1]^3 (+-0.15h jitter), %d "
@@ -683,7 +673,7 @@ def main():
                 "steps": steps, "warmup": warm, "ms_per_step": el * 1e3 / steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "config": ref_config,
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1,
                                  "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}

@@ -93,31 +93,8 @@ class Solver:
 
     # -- operator --------------------------------------------------------------
     def apply_k(self, x):
-        """K x with the assembled sparse operator.
-
-        A plain sparse matrix product: real operands go through PyTorch's CPU
-        CSR product (multi-threaded, each row summed in order), complex ones
-        (the complex-step derivatives of oracle.adjoint) through scipy's.  The
-        two agree to rounding; neither reorders anything beyond a row sum."""
-        K = self.asm.Kmat
-        if np.iscomplexobj(x) or np.iscomplexobj(K.data):
-            return K @ x
-        import torch
-        if getattr(self, "_kt", None) is None or self._kt_src is not K:
-            import warnings
-            with warnings.catch_warnings():
-                warnings.simplefilter("ignore")
-                self._kt = torch.sparse_csr_tensor(
-                    torch.from_numpy(K.indptr.astype(np.int64)),
-                    torch.from_numpy(K.indices.astype(np.int64)),
-                    torch.from_numpy(np.ascontiguousarray(K.data, dtype=np.float64)),
-                    size=K.shape, check_invariants=True)
-            self._kt_src = K
-        xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
-        squeeze = xt.dim() == 1
-        y = self._kt @ (xt[:, None] if squeeze else xt)
-        y = y.numpy()
-        return y[:, 0] if squeeze else y
+        """K x with the assembled sparse operator (scipy's CSR product)."""
+        return self.asm.Kmat @ x
 
     def source_vector(self, t):
         a = self.asm

@@ -199,6 +199,8 @@ class Solver(Plan):
         import torch
         self.torch = torch
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:   # the current device
+            self.device = torch.device("cuda", torch.cuda.current_device())
         dt = torch.float64 if self.precision == "fp64" else torch.float32
         self.dtype = dt
         i = self.info

@@ -8,9 +8,11 @@ differs.
 
 * jittered sphere: 3^3 jittered Kuhn grid (162 tets), p = 3, eps = 4 sphere,
   upwind, LSRK4, Gaussian pulse, dt = 5.859e-4, 1000 steps;
-* dipole in a PML: [-1,1]^3 on a 2^3 grid (48 tets, 42 in the layer), p = 4,
-  PML 0.25 thick, sigma_max 40, z dipole f0 = 2, from rest, dt = 6e-4,
-  2000 steps;
+* dipole in a PML: [-1,1]^3 on a 2^3 grid (48 tets), p = 4, z dipole f0 = 2,
+  from rest, dt = 6e-4, 2000 steps; the quadratic layer (sigma_max 40) starts
+  at |x| = 0.6 and is 0.4 thick, so that the replica's centroids (at 0.25,
+  0.5, 0.75 of a unit cube) fall in it -- with the full workload's 0.25-thick
+  layer at 0.75 no replica element would be damped;
 * inverse problem (forward records): [-1,1]^3 on a 2^3 grid, p = 3, the
   same PML, lognormal eps, 8 dipole columns, 32 receivers recording E after
   every step, dt = 1.5625e-3, 1500 steps.
@@ -100,7 +102,7 @@ def test_jittered_sphere_1000_steps(D, sphere_case, prec, tol, variant):
 
 
 # -- dipole in a PML -----------------------------------------------------------------
-PML = dict(lo=(-0.75,) * 3, hi=(0.75,) * 3, thickness=0.25, sigma_max=40.0, order=2)
+PML = dict(lo=(-0.6,) * 3, hi=(0.6,) * 3, thickness=0.4, sigma_max=40.0, order=2)
 
 
 @pytest.fixture(scope="module")
