@@ -227,7 +227,7 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     return out
 
 
-def run_pml(precision, steps, warmup, n=40, integrator="lsrk4"):
+def run_pml(precision, steps, warmup, n=40, integrator="lsrk4", variant=None, groups=None):
     """Dipole-in-PML workload: [-1,1]^3 on an n^3 Kuhn grid (384,000 tets at n=40),
     p=4, PML 0.25 thick with quadratic profile and sigma_max=40, z-directed
     dipole, starting from rest; upwind flux with LSRK4 or, with
@@ -245,7 +245,12 @@ def run_pml(precision, steps, warmup, n=40, integrator="lsrk4"):
                  stream=stream, pml=w.pml)
     g.set_sources(w.extra["sources"])
     tuned = None
-    if precision == "fp32" and integrator == "lsrk4":   # tile shape (state untouched)
+    if precision == "fp32" and integrator == "lsrk4" and variant is not None:
+        g.set_variant(variant)     # profiling runs: the shape the autotuner picks, pinned
+        if groups is not None:
+            g.set_tile_groups(groups)
+        tuned = {"variant": int(variant), "forced": True, "tile_groups": g.tile_groups()}
+    elif precision == "fp32" and integrator == "lsrk4":   # tile shape (state untouched)
         v, ms_v = g.autotune()
         tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms_v],
                  "tile_groups": g.tile_groups()}
@@ -378,6 +383,27 @@ def run_reflection(n=16, p=4, chunks=8, T=2.4, sigma_max=40.0):
     el_s = time.perf_counter() - start
     return dict(n=n, p=p, K_small=gs.K, K_large=gl.K, steps=per * chunks, T=tt,
                 reflection=diff / ref, seconds=el_s)
+
+
+def fp64_reference_rate(n=8192, reps=5):
+    """FP64 throughput reference of this GPU: cuBLAS DGEMM through torch.matmul
+    (2 n^3 flop per product, best of `reps` after a warm-up), CUDA events."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return dict(what="cuBLAS DGEMM %d^3 (torch.matmul, float64)" % n, ms=best,
+                tflops=2.0 * n ** 3 / (best * 1e-3) / 1e12)
 
 
 def run_cavity():
@@ -616,8 +642,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=32,
                     help="Kuhn grid size (32 = the benchmarked workload; smaller for profiling)")
-    ap.add_argument("--only", choices=["fp32", "fp64", "adjoint"], default=None,
-                    help="profile one precision (or the inverse-problem leg) only")
+    ap.add_argument("--only", choices=["fp32", "fp64", "adjoint", "pml"], default=None,
+                    help="profile one precision (or the inverse-problem or dipole-in-PML leg) only")
+    ap.add_argument("--pml-n", type=int, default=40,
+                    help="Kuhn grid size of the dipole-in-PML leg (40 = the benchmarked workload)")
     ap.add_argument("--adjoint-n", type=int, default=24,
                     help="Kuhn grid size of the inverse problem (24 = the benchmarked workload)")
     ap.add_argument("--no-pml", action="store_true", help="skip the p=4 dipole-in-PML workload")
@@ -683,6 +711,13 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
+    if args.only == "pml":
+        r = run_pml("fp32", args.pml_steps, args.warmup, n=args.pml_n, variant=args.variant,
+                    groups=args.tile_groups)
+        r.pop("_final")
+        if rank == 0:
+            print(json.dumps({"profile_run": "pml", **r}))
+        return
     if args.only == "adjoint":
         r = run_adjoint(args.adjoint_steps, args.adjoint_n)
         if rank == 0:
@@ -733,6 +768,9 @@ def main():
         "autotune": r32["tuned"],
         "clocks": r32["clocks"],
     }
+    if world == 1:
+        line["fp64"]["reference_rate"] = fp64_reference_rate()
+        line["fp64"]["flop_per_dof_update"] = 1450
     if not args.no_pml and world == 1:
         p32 = run_pml("fp32", args.pml_steps, 3)
         p64 = run_pml("fp64", args.pml_steps, 3)
