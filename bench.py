@@ -311,10 +311,16 @@ def run_batched(steps, warmup):
             [np.zeros((len(r), 2)), (np.sin(_m.pi * r[:, 0]) * np.sin(_m.pi * r[:, 1]))[:, None],
              np.zeros((len(r), 3))], axis=1))
         members.append(gc)
+    step_bytes = 0
     for m in members:
         v, ms = m.autotune()
         chosen.append(int(v))
         dofs += 6 * m.N * m.K * m.S
+        # algorithmic bytes of one LSRK4 step of the member (fields, PML auxiliaries, geometry)
+        field = 6 * m.N * m.K * m.S * 4
+        aux = 6 * m.N * m.npml * m.S * 4
+        geo = m.K * (16 * 4 + 4 * 4 + 4)
+        step_bytes += (3 * field + 3 * aux + geo) + 4 * (4 * field + 4 * aux + geo)
     b = D.Batch(members)
     b.advance(warmup)
     torch.cuda.synchronize(dev)
@@ -328,7 +334,10 @@ def run_batched(steps, warmup):
     ms = ev0.elapsed_time(ev1)
     for m in members:
         m.status()
+    hbm = _peaks().get("hbm_gbs", 6800.0)
     return dict(value=dofs * steps / (ms * 1e-3), ms_per_step=ms / steps, steps=steps,
+                bytes_per_step=step_bytes,
+                hbm_frac=step_bytes / (ms / steps * 1e-3) / 1e9 / hbm,
                 members=len(members), dofs_per_step=dofs, sources=w.S,
                 cavities=[(c.n, c.p) for c in cavs], variants=chosen,
                 graph_launches=steps // 2)
@@ -476,7 +485,13 @@ def run_adjoint(steps, n=24):
     torch.cuda.synchronize(dev)
     t2 = time.perf_counter()
     dofs = 6 * g.N * g.K * g.S
+    import ctypes
+    ws = ctypes.c_size_t()
+    D._lib.dgm_adjoint_workspace(g.handle, int(steps), ctypes.byref(ws))
+    seg = int(math.ceil(math.sqrt(steps / 5.0)))
     return dict(steps=steps, K=g.K, S=g.S, receivers=len(rec), loss=float(loss.detach()),
+                checkpoint_segment=seg, workspace_bytes=int(ws.value),
+                state_bytes=int(g.info.bytes_fields + g.info.bytes_aux),
                 forward_s=t1 - t0, adjoint_s=t2 - t1,
                 forward_dof_updates_per_s=dofs * steps / (t1 - t0),
                 adjoint_over_forward=(t2 - t1) / (t1 - t0),
@@ -650,14 +665,16 @@ def main():
                     help="Kuhn grid size of the inverse problem (24 = the benchmarked workload)")
     ap.add_argument("--no-pml", action="store_true", help="skip the p=4 dipole-in-PML workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
-    ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--batched-steps", type=int, default=1000,
+                    help="steps of the batched workload (1000, its stated step count)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the inverse-problem workload")
     ap.add_argument("--variant", type=int, default=None,
                     help="force the FP32 stage-kernel tile shape instead of autotuning "
                          "(profiling runs: the autotuner's timings are distorted under ncu)")
     ap.add_argument("--tile-groups", type=int, default=None,
                     help="with --variant: force the FP32 tile visiting order (default: plain order)")
-    ap.add_argument("--adjoint-steps", type=int, default=60)
+    ap.add_argument("--adjoint-steps", type=int, default=1500,
+                    help="steps of the inverse problem (1500, its stated step count)")
     ap.add_argument("--pml-steps", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
