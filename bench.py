@@ -394,6 +394,37 @@ def run_reflection(n=16, p=4, chunks=8, T=2.4, sigma_max=40.0):
                 reflection=diff / ref, seconds=el_s)
 
 
+def run_mixed(precision, steps, warmup, n=32, p=2):
+    """Mixed orders (E of degree p + 1, H of degree p; Sec. III) on the
+    jittered-sphere mesh (upwind, LSRK4, the same pulse), the plain
+    one-thread-per-column kernel.  DoFs per column: 3 (N_E + N_H) per element."""
+    import torch
+    from paper_2002_08733_gb300 import dgmax as D
+    w = W.jittered_sphere(n=n, p=p + 1)
+    xyz, tets, eps = build_problem(w)
+    dev = torch.device("cuda", 0)
+    g = D.Solver(xyz, tets, eps, 1.0, p, precision, "upwind", "lsrk4", w.dt, device=dev,
+                 mixed=True)
+    g.project(pulse(w.extra["r0"]))
+    t = 0.0
+    for _ in range(warmup):
+        g.advance(1, t)
+        t += w.dt
+    torch.cuda.synchronize(dev)
+    st = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    g.advance(steps, t)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    g.status()
+    dofs = 3 * (g.N + g.NH) * g.K
+    return dict(precision=precision, K=g.K, p_E=p + 1, p_H=p, N_E=g.N, N_H=g.NH, steps=steps,
+                ms_per_step=ms / steps, value=dofs * steps / (ms * 1e-3))
+
+
 def fp64_reference_rate(n=8192, reps=5):
     """FP64 throughput reference of this GPU: cuBLAS DGEMM through torch.matmul
     (2 n^3 flop per product, best of `reps` after a warm-up), CUDA events."""
@@ -657,7 +688,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=32,
                     help="Kuhn grid size (32 = the benchmarked workload; smaller for profiling)")
-    ap.add_argument("--only", choices=["fp32", "fp64", "adjoint", "pml"], default=None,
+    ap.add_argument("--only", choices=["fp32", "fp64", "adjoint", "pml", "mixed"], default=None,
                     help="profile one precision (or the inverse-problem or dipole-in-PML leg) only")
     ap.add_argument("--pml-n", type=int, default=40,
                     help="Kuhn grid size of the dipole-in-PML leg (40 = the benchmarked workload)")
@@ -676,6 +707,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=1500,
                     help="steps of the inverse problem (1500, its stated step count)")
     ap.add_argument("--pml-steps", type=int, default=20)
+    ap.add_argument("--mixed-steps", type=int, default=10)
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-order leg")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -728,6 +761,11 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
+    if args.only == "mixed":
+        r = [run_mixed(pr, args.mixed_steps, args.warmup, n=args.n) for pr in ("fp32", "fp64")]
+        if rank == 0:
+            print(json.dumps({"profile_run": "mixed", "runs": r}))
+        return
     if args.only == "pml":
         r = run_pml("fp32", args.pml_steps, args.warmup, n=args.pml_n, variant=args.variant,
                     groups=args.tile_groups)
@@ -808,6 +846,13 @@ def main():
                                         "cavities n 6..28, p 2..5; FP32; one graph launch per "
                                         "two steps; autotuned tile shapes",
                                **run_batched(args.batched_steps, 2))
+    if not args.no_mixed and world == 1:
+        line["mixed_orders"] = dict(
+            workload="jittered sphere mesh (%d^3, %d tets), E of degree 3 and H of degree 2 "
+                     "(Sec. III), upwind, LSRK4, the same pulse; plain one-thread-per-column "
+                     "kernel with dense operators" % (args.n, w.K),
+            fp32=run_mixed("fp32", args.mixed_steps, 2, n=args.n),
+            fp64=run_mixed("fp64", min(args.mixed_steps, 3), 1, n=args.n))
     if world == 1:
         line["cavity"] = dict(workload="PEC cavity 4^3 (384 tets), p=2, central, leapfrog, "
                                        "TM110, 200 steps (latency regime, state fits in L2)",

@@ -97,7 +97,7 @@ typedef struct {
     size_t bytes_aux;     /* one auxiliary buffer: 6 N n_pml S reals (0 without PML) */
     size_t bytes_geom;    /* geometry + workspace buffer, 256-byte aligned start */
     int32_t n_quad;       /* projection quadrature points per element */
-    int32_t reserved;
+    int32_t N_H;          /* modes per H component: N, except on a mixed-order plan */
 } dgm_info;
 
 /* Create a plan: validates the mesh, sorts each element's vertices, builds the
@@ -109,6 +109,20 @@ typedef struct {
 int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt,
                     const int64_t* tets, const double* eps, const double* mu,
                     const dgm_pml* pml, const dgm_options* opt);
+
+/* Mixed orders (Sec. III, Eqs. (triale)/(trialh)): E of degree opt->p + 1 and
+ * H of degree opt->p, as the paper discretises them.  Every operator is a
+ * submatrix of the degree-(p+1) reference operators (hierarchical orthonormal
+ * bases; checked at creation).  Field buffers hold E component c, mode l at row
+ * c N + l (N = dgm_info.N, E's modes) and H component c, mode l at row
+ * 3 N + c N_H + l; bytes_fields covers 3 (N + N_H) rows.  Supports LSRK4 (and
+ * dgm_rhs) with central or upwind flux, FP64 and FP32, p = 1..3, sources,
+ * receivers, projection, energy and partitions; no PML, leapfrog, adjoint or
+ * batch (DGM_EUNSUP / DGM_EINVAL).  Runs a plain one-thread-per-column kernel
+ * with dense operators.  Otherwise as dgm_plan_create. */
+int dgm_plan_create_mixed(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt,
+                          const int64_t* tets, const double* eps, const double* mu,
+                          const dgm_pml* pml, const dgm_options* opt);
 
 /* Sizes and counts of a plan.  No CUDA call. */
 int dgm_plan_info(const dgm_plan* plan, dgm_info* out);

@@ -128,13 +128,16 @@ struct dgm_plan {
     dgm_options opt;
     HostMesh mesh;
     const KernelTable* kt = nullptr;
-    std::vector<double> S, R;   // reference matrices (FP64)
-    int N = 0, NF = 0;
+    std::vector<double> S, R;   // reference matrices (FP64), degree pE
+    int N = 0, NF = 0;          // modes per component (E's on a mixed-order plan)
+    int mixed = 0;              // E of degree p + 1, H of degree p (dgm_plan_create_mixed)
+    int pE = 0;                 // degree of E (= opt.p unless mixed)
+    int NH = 0, NFH = 0;        // modes per H component (= N, NF unless mixed)
     bool has_pml = false;
     // geometry buffer layout (byte offsets)
     size_t off_geo = 0, off_nbr = 0, off_pml = 0, off_src = 0, off_part = 0, off_status = 0,
            off_rec = 0, off_time = 0, off_geo32 = 0, off_fnb = 0, off_fnb32 = 0, off_tcb = 0,
-           bytes_tcb = 0, bytes_geom = 0;
+           bytes_tcb = 0, off_ops = 0, bytes_ops = 0, bytes_geom = 0;
     int n_rec = 0;
     std::vector<double> src_host;   // S * (SRC_HDR + 3N)
     bool have_src = false;
@@ -175,7 +178,7 @@ int partition_fail(int code, const std::string& msg) { return fail(code, msg); }
 template <typename R>
 __global__ void __launch_bounds__(ENERGY_THREADS)
 energy_partial(const R* __restrict__ u, const double* __restrict__ geo, int64_t K, int64_t Kact,
-               int S, int N, double* __restrict__ part) {
+               int S, int N, int NH, double* __restrict__ part) {
     __shared__ double red[ENERGY_THREADS];
     const int s = blockIdx.y;
     const int64_t C = K * S;
@@ -191,11 +194,13 @@ energy_partial(const R* __restrict__ u, const double* __restrict__ geo, int64_t 
         const double mat[2] = {geo[int64_t(G_EPS) * K + e], geo[int64_t(G_MU) * K + e]};
         const int64_t col = e * S + s;
         double w = 0.0;
-        for (int fld = 0; fld < 2; ++fld) {
+        for (int fld = 0; fld < 2; ++fld) {   // E rows c N + l, H rows 3 N + c NH + l
             double wf = 0.0;
-            for (int l = 0; l < N; ++l) {
+            const int nm = fld == 0 ? N : NH;
+            for (int l = 0; l < nm; ++l) {
                 double v[3];
-                for (int j = 0; j < 3; ++j) v[j] = double(u[int64_t((3 * fld + j) * N + l) * C + col]);
+                for (int j = 0; j < 3; ++j)
+                    v[j] = double(u[int64_t(fld == 0 ? j * N + l : 3 * N + j * NH + l) * C + col]);
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j < 3; ++j) wf += v[i] * G[i][j] * v[j];
             }
@@ -249,9 +254,9 @@ extern "C" {
 
 const char* dgm_last_error(void) { return g_err.c_str(); }
 
-int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, const int64_t* tets,
-                    const double* eps, const double* mu, const dgm_pml* pml,
-                    const dgm_options* opt) {
+static int plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, const int64_t* tets,
+                       const double* eps, const double* mu, const dgm_pml* pml,
+                       const dgm_options* opt, int mixed) {
     if (!out || !opt) return fail(DGM_EINVAL, "null plan pointer or options");
     *out = nullptr;
     if (opt->n_columns < 1) return fail(DGM_EINVAL, "n_columns must be >= 1");
@@ -261,7 +266,11 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
         return fail(DGM_EINVAL, "unknown integrator");
     if (opt->integrator == DGM_LEAPFROG && opt->flux != DGM_CENTRAL)
         return fail(DGM_EUNSUP, "leapfrog needs the central flux");
-    const KernelTable* kt = kernel_table(opt->p, opt->precision);
+    const int pE = mixed ? opt->p + 1 : opt->p;
+    if (mixed && (pml || opt->integrator != DGM_LSRK4))
+        return fail(DGM_EUNSUP, "mixed-order plans support LSRK4 without a PML");
+    const KernelTable* kt = mixed ? kernel_table_mixed(pE, opt->precision)
+                                  : kernel_table(opt->p, opt->precision);
     if (!kt) return fail(DGM_EUNSUP, "unsupported polynomial degree / precision");
     if (pml) {
         if (!(pml->thickness > 0.0) || !(pml->sigma_max >= 0.0) || pml->order < 0)
@@ -272,8 +281,12 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
     dgm_plan* P = new dgm_plan();
     P->opt = *opt;
     P->kt = kt;
-    P->N = nmodes(opt->p);
-    P->NF = nfmodes(opt->p);
+    P->mixed = mixed;
+    P->pE = pE;
+    P->N = nmodes(pE);
+    P->NF = nfmodes(pE);
+    P->NH = nmodes(opt->p);
+    P->NFH = nfmodes(opt->p);
     P->has_pml = pml != nullptr;
     std::string err;
     int rc = build_mesh(nv, xyz, nt, tets, eps, mu, pml ? pml->lo : nullptr, pml ? pml->hi : nullptr,
@@ -283,11 +296,32 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
         delete P;
         return fail(rc, err);
     }
-    if (build_refmats(opt->p, P->S, P->R, err)) {
+    if (build_refmats(pE, P->S, P->R, err)) {
         delete P;
         return fail(DGM_EINVAL, err);
     }
-    {   // the kernels carry the reference operators as compiled literals: check them
+    if (mixed) {   // H's operators must be the leading submatrices of E's (hierarchical bases)
+        std::vector<double> Sh, Rh;
+        if (build_refmats(opt->p, Sh, Rh, err)) {
+            delete P;
+            return fail(DGM_EINVAL, err);
+        }
+        const int N = P->N, NF = P->NF, NH = P->NH, NFH = P->NFH;
+        double worst = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int l = 0; l < NH; ++l)
+                for (int m = 0; m < NH; ++m)
+                    worst = std::fmax(worst, std::fabs(Sh[(a * NH + l) * NH + m] - P->S[(a * N + l) * N + m]));
+        for (int f = 0; f < 4; ++f)
+            for (int m = 0; m < NFH; ++m)
+                for (int l = 0; l < NH; ++l)
+                    worst = std::fmax(worst, std::fabs(Rh[(f * NFH + m) * NH + l] - P->R[(f * NF + m) * N + l]));
+        if (!(worst <= 1e-12)) {
+            delete P;
+            return fail(DGM_EINVAL, "degree-p operators are not submatrices of degree p + 1");
+        }
+    }
+    if (!mixed) {   // the kernels carry the reference operators as compiled literals: check them
         const double* cs = ref_S_compiled(opt->p);
         const double* cr = ref_R_compiled(opt->p);
         double worst = 0.0, scale = 0.0;
@@ -334,15 +368,31 @@ int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, c
     P->off_rec = off;
     off = align256(off + sizeof(double) * size_t(opt->max_receivers) * (REC_HDR + 9 * P->N));
     // operator image of the tensor-core stage variant (FP32, p = 2, 3)
-    P->bytes_tcb = opt->precision == DGM_FP32 ? tc_image_bytes(opt->p) : 0;
+    P->bytes_tcb = (opt->precision == DGM_FP32 && !mixed) ? tc_image_bytes(opt->p) : 0;
     P->off_tcb = off;
     off = align256(off + P->bytes_tcb);
+    // dense reference operators of a mixed-order plan (S then R, degree p + 1)
+    P->bytes_ops = mixed ? (P->S.size() + P->R.size()) * size_t(kt->real_size) : 0;
+    P->off_ops = off;
+    off = align256(off + P->bytes_ops);
     P->bytes_geom = off;
     P->k_active = K;
     P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
     for (int s = 0; s < Sc; ++s) P->src_host[size_t(s) * (SRC_HDR + 3 * P->N)] = -1.0;
     *out = P;
     return DGM_OK;
+}
+
+int dgm_plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt, const int64_t* tets,
+                    const double* eps, const double* mu, const dgm_pml* pml,
+                    const dgm_options* opt) {
+    return plan_create(out, nv, xyz, nt, tets, eps, mu, pml, opt, 0);
+}
+
+int dgm_plan_create_mixed(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt,
+                          const int64_t* tets, const double* eps, const double* mu,
+                          const dgm_pml* pml, const dgm_options* opt) {
+    return plan_create(out, nv, xyz, nt, tets, eps, mu, pml, opt, 1);
 }
 
 void dgm_plan_destroy(dgm_plan* plan) { delete plan; }
@@ -356,10 +406,11 @@ int dgm_plan_info(const dgm_plan* P, dgm_info* out) {
     out->NF = P->NF;
     out->S = P->opt.n_columns;
     out->real_size = P->kt->real_size;
-    out->bytes_fields = size_t(6) * P->N * P->mesh.K * P->opt.n_columns * P->kt->real_size;
+    out->bytes_fields = size_t(3) * (P->N + P->NH) * P->mesh.K * P->opt.n_columns * P->kt->real_size;
     out->bytes_aux = size_t(6) * P->N * P->mesh.npml * P->opt.n_columns * P->kt->real_size;
     out->bytes_geom = P->bytes_geom;
-    out->n_quad = (P->opt.p + 3) * (P->opt.p + 3) * (P->opt.p + 3);
+    out->n_quad = (P->pE + 3) * (P->pE + 3) * (P->pE + 3);
+    out->N_H = P->NH;
     return DGM_OK;
 }
 
@@ -450,6 +501,18 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
                                  cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_fail(e, "upload tensor-core operator image");
     }
+    std::vector<unsigned char> ops(P->bytes_ops);
+    if (P->bytes_ops) {
+        const size_t n = P->S.size() + P->R.size();
+        for (size_t i = 0; i < n; ++i) {
+            const double v = i < P->S.size() ? P->S[i] : P->R[i - P->S.size()];
+            if (P->kt->real_size == 8) std::memcpy(ops.data() + 8 * i, &v, 8);
+            else { const float f = float(v); std::memcpy(ops.data() + 4 * i, &f, 4); }
+        }
+        if ((e = cudaMemcpyAsync(P->geom + P->off_ops, ops.data(), ops.size(), cudaMemcpyHostToDevice,
+                                 st)) != cudaSuccess)
+            return cuda_fail(e, "upload mixed-order operators");
+    }
     if (int rc = build_face_table(P)) return rc;
     // the host copies above are pageable: finish them before the host vectors can change
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
@@ -478,6 +541,7 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.tile_groups = P->tile_groups;
     prm.tc_b = P->bytes_tcb ? static_cast<const void*>(P->geom + P->off_tcb) : nullptr;
     prm.K_active = P->k_active;
+    prm.ops = P->bytes_ops ? static_cast<const void*>(P->geom + P->off_ops) : nullptr;
 }
 
 int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double* pos,
@@ -519,7 +583,7 @@ int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double*
         out[2] = bw[i];
         out[3] = t0[i];
         std::vector<double> phi(N);
-        ref_basis_values(P->opt.p, xr, phi.data());
+        ref_basis_values(P->pE, xr, phi.data());
         // w_{j,l} = dir . (A^-T e_j) phi_l(r_hat) = sum_c Ait[c][j] dir_c phi_l
         for (int j = 0; j < 3; ++j) {
             double dj = 0.0;
@@ -570,7 +634,7 @@ int dgm_set_receivers(dgm_plan* P, int32_t n, const double* pos) {
         if (e < 0) return fail(DGM_EINVAL, "receiver point outside the mesh");
         double* w = &host[i * rec];
         w[0] = double(e);
-        ref_basis_values(P->opt.p, xr, phi.data());
+        ref_basis_values(P->pE, xr, phi.data());
         for (int c = 0; c < 3; ++c)
             for (int j = 0; j < 3; ++j)
                 for (int l = 0; l < N; ++l)
@@ -733,7 +797,7 @@ static int halo_copy_launch(dgm_plan* P, void* fields, const int64_t* idx, int64
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (n < 0 || (n > 0 && (!fields || !idx || !buf))) return fail(DGM_EINVAL, "null halo argument");
     if (n == 0) return DGM_OK;
-    const int rows = 6 * P->N, S = P->opt.n_columns;
+    const int rows = 3 * (P->N + P->NH), S = P->opt.n_columns;
     const int64_t total = n * S * rows;
     const unsigned grid = unsigned((total + 255) / 256);
     int32_t* status = reinterpret_cast<int32_t*>(P->geom + P->off_status);
@@ -784,10 +848,10 @@ int dgm_energy(dgm_plan* P, const void* fields, double* out) {
     dim3 grid(ENERGY_BLOCKS, Sc);
     if (P->kt->real_size == 8)
         energy_partial<double><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const double*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
+            static_cast<const double*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, P->NH, part);
     else
         energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const float*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
+            static_cast<const float*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, P->NH, part);
     energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(
         part, ENERGY_BLOCKS, Sc, res, reinterpret_cast<int32_t*>(P->geom + P->off_status));
     cudaError_t e = cudaGetLastError();
@@ -813,7 +877,7 @@ int dgm_pml_elements(const dgm_plan* P, int64_t* out) {
 int dgm_quad_points(const dgm_plan* P, double* xyz_out) {
     if (!P || !xyz_out) return fail(DGM_EINVAL, "null argument");
     std::vector<double> pts, w;
-    tet_rule(P->opt.p + 3, pts, w);
+    tet_rule(P->pE + 3, pts, w);
     const size_t nq = w.size();
     const int64_t K = P->mesh.K;
     for (int64_t e = 0; e < K; ++e) {
@@ -832,22 +896,24 @@ int dgm_project(dgm_plan* P, const double* samples, int32_t column, void* fields
     if (!samples || !fields || column < 0 || column >= P->opt.n_columns)
         return fail(DGM_EINVAL, "invalid projection arguments");
     std::vector<double> pts, w;
-    tet_rule(P->opt.p + 3, pts, w);
+    tet_rule(P->pE + 3, pts, w);
     const size_t nq = w.size();
     const int64_t K = P->mesh.K;
     const int N = P->N;
     std::vector<double> phi(nq * N);
-    for (size_t q = 0; q < nq; ++q) ref_basis_values(P->opt.p, &pts[3 * q], &phi[q * N]);
+    for (size_t q = 0; q < nq; ++q) ref_basis_values(P->pE, &pts[3 * q], &phi[q * N]);
     // covariant coefficients u_l = A^T sum_q w_q phi_l(q) f(r_q)  (closed-form block mass inverse)
     const int rs = P->kt->real_size;
-    std::vector<unsigned char> host(size_t(6) * N * K * rs);
+    const int NH = P->NH;   // H keeps its first NH modes (the projection onto its own space)
+    const size_t rows = size_t(3) * (N + NH);
+    std::vector<unsigned char> host(rows * K * rs);
     for (int64_t e = 0; e < K; ++e) {
         double AT[3][3];   // A^T[j][r] = edge j, coordinate r
         const double* V = &P->mesh.verts[12 * e];
         for (int j = 0; j < 3; ++j)
             for (int r = 0; r < 3; ++r) AT[j][r] = V[3 * (j + 1) + r] - V[r];
         for (int fld = 0; fld < 2; ++fld)
-            for (int l = 0; l < N; ++l) {
+            for (int l = 0; l < (fld == 0 ? N : NH); ++l) {
                 double m[3] = {0, 0, 0};
                 for (size_t q = 0; q < nq; ++q) {
                     const double* f = &samples[(e * nq + q) * 6 + 3 * fld];
@@ -855,7 +921,7 @@ int dgm_project(dgm_plan* P, const double* samples, int32_t column, void* fields
                 }
                 for (int j = 0; j < 3; ++j) {
                     const double v = AT[j][0] * m[0] + AT[j][1] * m[1] + AT[j][2] * m[2];
-                    const size_t idx = size_t((3 * fld + j) * N + l) * K + e;
+                    const size_t idx = size_t(fld == 0 ? j * N + l : 3 * N + j * NH + l) * K + e;
                     if (rs == 8)
                         reinterpret_cast<double*>(host.data())[idx] = v;
                     else
@@ -865,7 +931,7 @@ int dgm_project(dgm_plan* P, const double* samples, int32_t column, void* fields
     }
     const int Sc = P->opt.n_columns;
     cudaError_t e = cudaMemcpy2DAsync(static_cast<unsigned char*>(fields) + size_t(column) * rs,
-                                      size_t(Sc) * rs, host.data(), rs, rs, size_t(6) * N * K,
+                                      size_t(Sc) * rs, host.data(), rs, rs, rows * K,
                                       cudaMemcpyHostToDevice, P->stream);
     if (e != cudaSuccess) return cuda_fail(e, "projection copy");
     e = cudaStreamSynchronize(P->stream);
@@ -940,10 +1006,10 @@ extern "C" int dgm_energy_noalloc(dgm_plan* P, const void* fields, double* out_d
     dim3 grid(ENERGY_BLOCKS, Sc);
     if (P->kt->real_size == 8)
         energy_partial<double><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const double*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
+            static_cast<const double*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, P->NH, part);
     else
         energy_partial<float><<<grid, ENERGY_THREADS, 0, P->stream>>>(
-            static_cast<const float*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, part);
+            static_cast<const float*>(fields), geo, P->mesh.K, P->k_active, Sc, P->N, P->NH, part);
     energy_final<<<(Sc + 127) / 128, 128, 0, P->stream>>>(
         part, ENERGY_BLOCKS, Sc, out_device, reinterpret_cast<int32_t*>(P->geom + P->off_status));
     e = cudaGetLastError();
@@ -1010,6 +1076,7 @@ extern "C" int dgm_batch_create(dgm_batch** out, dgm_plan* const* members, int32
         if (members[i]->opt.integrator != DGM_LSRK4) return fail(DGM_EINVAL, "batch members must use LSRK4");
         if (members[i]->k_active < members[i]->mesh.K)
             return fail(DGM_EINVAL, "batch members must have every element active (no halo)");
+        if (members[i]->mixed) return fail(DGM_EUNSUP, "mixed-order plans are not batched");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(DGM_EINVAL, "duplicate batch member");
     }
@@ -1224,6 +1291,7 @@ static int copy_state(dgm_plan* P, StateRef dst, const void* f, const void* a, c
 
 extern "C" int dgm_forward_record(dgm_plan* P, int64_t n_steps, double t0, double* records, void* ws_) {
     if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
+    if (P && P->mixed) return fail(DGM_EUNSUP, "the adjoint is not built for mixed-order plans");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (P->opt.integrator != DGM_LSRK4) return fail(DGM_EUNSUP, "the adjoint needs LSRK4");
     if (!records || !ws_ || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
@@ -1289,6 +1357,7 @@ static int axpby(dgm_plan* P, StateRef y, StateRef x, double a, double b, const 
 extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double* drec, void* ws_,
                            double* deps, double* dmu) {
     if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
+    if (P && P->mixed) return fail(DGM_EUNSUP, "the adjoint is not built for mixed-order plans");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (!drec || !ws_ || !deps || !dmu || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
     if (reinterpret_cast<uintptr_t>(ws_) % 256) return fail(DGM_EINVAL, "workspace must be 256-byte aligned");

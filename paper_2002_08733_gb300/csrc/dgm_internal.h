@@ -108,6 +108,7 @@ struct StageParams {
     int32_t tile_groups;  // tile visiting order: G interleaved segments (1: in order)
     const void* tc_b;     // tensor-core variant: B operand image (TcShape<P>::B_BYTES), or null
     int64_t K_active;     // elements updated: the first K_active (the rest are halo copies)
+    const void* ops;      // mixed-order plans: dense reference operators S, R of degree p + 1
 };
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms
@@ -146,6 +147,8 @@ struct KernelTable {
 };
 
 const KernelTable* kernel_table(int p, int precision);
+// Mixed-order plans (E of degree pE, H of degree pE - 1; dgm_mixed.cu).
+const KernelTable* kernel_table_mixed(int pE, int precision);
 
 // Host setup (dgm_setup.cpp)
 struct HostMesh {

@@ -52,7 +52,7 @@ class Info(ctypes.Structure):
                 ("NF", ctypes.c_int32), ("S", ctypes.c_int32), ("real_size", ctypes.c_int32),
                 ("bytes_fields", ctypes.c_size_t), ("bytes_aux", ctypes.c_size_t),
                 ("bytes_geom", ctypes.c_size_t), ("n_quad", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("N_H", ctypes.c_int32)]
 
 
 _lib = None
@@ -61,6 +61,8 @@ _P = ctypes.c_void_p
 _SIGS = {
     "dgm_plan_create": [ctypes.POINTER(_P), ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P,
                         ctypes.POINTER(Pml), ctypes.POINTER(Options)],
+    "dgm_plan_create_mixed": [ctypes.POINTER(_P), ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P,
+                              ctypes.POINTER(Pml), ctypes.POINTER(Options)],
     "dgm_plan_info": [_P, ctypes.POINTER(Info)],
     "dgm_bind": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
     "dgm_set_sources": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
@@ -139,7 +141,8 @@ class Plan:
     """Host-side plan (mesh setup, reference matrices); no GPU needed."""
 
     def __init__(self, xyz, tets, eps, mu, p, precision="fp64", flux="upwind",
-                 integrator="lsrk4", dt=1e-3, S=1, pml=None, max_receivers=0):
+                 integrator="lsrk4", dt=1e-3, S=1, pml=None, max_receivers=0, mixed=False):
+        """mixed=True: E of degree p + 1, H of degree p (dgm_plan_create_mixed)."""
         lib = load_library()
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         tets = np.ascontiguousarray(tets, dtype=np.int64)
@@ -159,9 +162,11 @@ class Plan:
             pm.sigma_max = pml["sigma_max"]
             pm.order = pml.get("order", 2)
         h = _P()
-        _check(lib.dgm_plan_create(ctypes.byref(h), xyz.shape[0], xyz.ctypes.data, K,
-                                   tets.ctypes.data, self.eps.ctypes.data, self.mu.ctypes.data,
-                                   ctypes.byref(pm) if pm is not None else None, ctypes.byref(opt)))
+        create = lib.dgm_plan_create_mixed if mixed else lib.dgm_plan_create
+        _check(create(ctypes.byref(h), xyz.shape[0], xyz.ctypes.data, K,
+                      tets.ctypes.data, self.eps.ctypes.data, self.mu.ctypes.data,
+                      ctypes.byref(pm) if pm is not None else None, ctypes.byref(opt)))
+        self.mixed = bool(mixed)
         self.handle = h
         self.opt = opt
         self.precision = precision
@@ -169,6 +174,7 @@ class Plan:
         _check(lib.dgm_plan_info(h, ctypes.byref(info)))
         self.info = info
         self.K, self.N, self.S, self.npml = info.K, info.N, info.S, info.n_pml
+        self.NH = info.N_H
         self.p = p
         self.dt = dt
 
@@ -204,7 +210,10 @@ class Solver(Plan):
         dt = torch.float64 if self.precision == "fp64" else torch.float32
         self.dtype = dt
         i = self.info
-        shape = (6, self.N, self.K, self.S)
+        # field buffer: rows (component, mode) -- 6 N of them, or 3 N + 3 N_H on a
+        # mixed-order plan -- by (element, column)
+        shape = (6, self.N, self.K, self.S) if not self.mixed else \
+            (3 * (self.N + self.NH), self.K, self.S)
         self.geom = torch.empty(i.bytes_geom + 256, dtype=torch.uint8, device=self.device)
         off = (-self.geom.data_ptr()) % 256
         self.geom_view = self.geom[off:off + i.bytes_geom]
@@ -224,8 +233,16 @@ class Solver(Plan):
                              _ptr(self.aux[1]), _ptr(self.aux_res), self.stream.cuda_stream))
 
     # -- layout conversion between (K, S, 6, N) and the device layout [6][N][K][S]
+    #    (mixed-order plans: H modes l >= N_H of the (K, S, 6, N) array are zero)
     def to_device(self, u):
-        t = self.torch.as_tensor(np.ascontiguousarray(np.transpose(np.asarray(u), (2, 3, 0, 1))))
+        u = np.asarray(u)
+        if self.mixed and u.shape[2] == 6:
+            rows = np.concatenate([u[:, :, 0:3, :].reshape(u.shape[0], u.shape[1], -1),
+                                   u[:, :, 3:6, :self.NH].reshape(u.shape[0], u.shape[1], -1)],
+                                  axis=2)                               # (K, S, rows)
+            t = self.torch.as_tensor(np.ascontiguousarray(np.transpose(rows, (2, 0, 1))))
+            return t.to(device=self.device, dtype=self.dtype).contiguous()
+        t = self.torch.as_tensor(np.ascontiguousarray(np.transpose(u, (2, 3, 0, 1))))
         return t.to(device=self.device, dtype=self.dtype).contiguous()
 
     def aux_to_device(self, aux_full):
@@ -233,9 +250,17 @@ class Solver(Plan):
         idx = self.pml_elements()
         return self.to_device(np.asarray(aux_full)[idx])
 
-    @staticmethod
-    def from_device(t):
-        return np.transpose(t.double().cpu().numpy(), (2, 3, 0, 1)).copy()
+    def from_device(self, t):
+        a = t.double().cpu().numpy()
+        if a.ndim == 3:   # mixed-order rows -> (K, S, 6, N) with H modes >= N_H zero
+            N, NH = self.N, self.NH
+            K, S = a.shape[1], a.shape[2]
+            out = np.zeros((K, S, 6, N))
+            r = np.transpose(a, (1, 2, 0))
+            out[:, :, 0:3, :] = r[:, :, :3 * N].reshape(K, S, 3, N)
+            out[:, :, 3:6, :NH] = r[:, :, 3 * N:].reshape(K, S, 3, NH)
+            return out
+        return np.transpose(a, (2, 3, 0, 1)).copy()
 
 
     def current(self):
@@ -427,7 +452,8 @@ class Solver(Plan):
         f = self.fields[self.current()] if fields is None else fields
         n = int(idx_device.numel())
         if out is None:
-            out = self.torch.empty((6 * self.N, n, self.S), dtype=self.dtype, device=self.device)
+            out = self.torch.empty((3 * (self.N + self.NH), n, self.S), dtype=self.dtype,
+                                   device=self.device)
         _check(_lib.dgm_halo_pack(self.handle, _ptr(f), _ptr(idx_device), n, _ptr(out)))
         return out
 
@@ -624,7 +650,7 @@ class PartitionedSolver:
             unpack=lambda q, b: g.halo_unpack(self.recv_idx[q], b),
             isend=lambda b, peer: dist.isend(b, peer),
             irecv=lambda b, peer: dist.irecv(b, peer),
-            empty_like_recv=lambda q: torch.empty((6 * g.N, len(self.halo.recv[q]), g.S),
+            empty_like_recv=lambda q: torch.empty((3 * (g.N + g.NH), len(self.halo.recv[q]), g.S),
                                                   dtype=g.dtype, device=g.device))
 
     def advance(self, n_steps, t0=0.0):

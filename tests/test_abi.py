@@ -157,3 +157,26 @@ def test_energy_noalloc_rejects_bad_output_buffers(lib, monkeypatch):
     with pytest.raises(ValueError):   # fields of the wrong precision
         g.energy_noalloc(FakeCuda(torch.float64, 4), fields=FakeCuda(torch.float64, 6 * 96))
     assert calls == []
+
+
+def test_mixed_order_plan_sizes_and_limits(lib):
+    """dgm_plan_create_mixed: E of degree p + 1, H of degree p -- field rows
+    3 N + 3 N_H; no PML, no leapfrog, p <= 3."""
+    from paper_2002_08733_gb300 import dgmax as D
+    xyz, tets = W.kuhn_mesh(2)
+    for p, prec, rs in ((1, "fp64", 8), (2, "fp32", 4), (3, "fp64", 8)):
+        pl = D.Plan(xyz, tets, 1.0, 1.0, p, prec, "upwind", "lsrk4", 1e-3, S=2, mixed=True)
+        NE, NH = W.n_modes(p + 1), W.n_modes(p)
+        assert (pl.info.N, pl.info.N_H) == (NE, NH)
+        assert pl.info.bytes_fields == 3 * (NE + NH) * 48 * 2 * rs
+        assert pl.info.n_quad == (p + 4) ** 3
+    plain = D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", "upwind", "lsrk4", 1e-3)
+    assert plain.info.N_H == plain.info.N
+    pml = dict(lo=(0.25,) * 3, hi=(0.75,) * 3, thickness=0.25, sigma_max=10.0)
+    for kw in (dict(pml=pml), dict(integrator="leapfrog", flux="central"), dict(p=4)):
+        args = dict(p=2, precision="fp64", flux="upwind", integrator="lsrk4", dt=1e-3)
+        args.update(kw)
+        extra = {"pml": args.pop("pml")} if "pml" in args else {}
+        with pytest.raises(D.DgmError):
+            D.Plan(xyz, tets, 1.0, 1.0, args["p"], args["precision"], args["flux"],
+                   args["integrator"], args["dt"], mixed=True, **extra)
