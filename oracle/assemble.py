@@ -79,9 +79,17 @@ class Assembly:
         subset, the operator maps the full state to those elements' rows
         only, which lets the oracle evaluate the right-hand side of sampled
         elements of a mesh too large to assemble whole.
+    incident: boundary faces through which an incident field enters, as a
+        list of vertex-id triples, or None.  On those faces the exterior
+        state is e+ = e- + 2 E_inc, h+ = -h-, Z+ = Z-: the listing of Appendix A
+        sets the boundary value of e to 2 E_inc + e and builds the E equation as
+        the transpose of the H equation's operator, which leaves no E-equation
+        boundary term, i.e. tangential h* = 0 (a magnetic wall radiating the
+        incident field).  Operator terms: only the upwind H-H term
+        Z (phi, n x (n x h)); the rest is a forcing (Solver.incident_vector).
     """
 
-    def __init__(self, mesh, p, eps, mu, flux="central", sigma=None, rows=None):
+    def __init__(self, mesh, p, eps, mu, flux="central", sigma=None, rows=None, incident=None):
         self.mesh = mesh
         self.rows = np.arange(mesh.K) if rows is None else np.asarray(rows, dtype=np.int64)
         self.R = self.rows.size
@@ -100,6 +108,17 @@ class Assembly:
         self.flux = flux
         self.has_pml = sigma is not None
         self.sigma = None if sigma is None else np.asarray(sigma, dtype=np.float64)
+        self.incident = set()
+        if incident is not None:
+            keys = {}
+            for T in range(mesh.K):
+                for f in range(4):
+                    keys[tuple(np.delete(mesh.tets[T], f))] = (T, f)
+            for tri in incident:
+                T, f = keys[tuple(sorted(int(v) for v in tri))]
+                if mesh.nbr[T, f] >= 0:
+                    raise ValueError("incident face %s is not a boundary face" % (tri,))
+                self.incident.add((T, f))
         self._volume()
         self._faces()
         self._global()
@@ -213,6 +232,10 @@ class Assembly:
             put(H, T, E, T, -self.C_eh[i].T)
         for ent in self.face:
             T, nb = ent["T"], ent["nb"]
+            if nb < 0 and (T, ent["f"]) in self.incident:   # e+ = e- + 2 E_inc, h+ = -h-
+                if upwind:   # n x (e* - e-) = n x E_inc - Z n x (n x h-)
+                    put(H, T, H, T, Z[T] * ent["xx_own"])
+                continue
             if nb < 0:   # PEC wall: e+ = -e-, h+ = h-
                 put(E, T, H, T, ent["x_own"])
                 if upwind:

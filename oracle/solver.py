@@ -107,11 +107,55 @@ class Solver:
             f[r0:r0 + a.n3, s] -= g * w
         return f
 
+    def set_incident(self, E0, direction, speed, f0, bw, t0, quad=None):
+        """Incident plane wave E_inc(r, t) = E0 g(t - t0 - d . r / speed),
+        g(tau) = cos(2 pi f0 tau) exp(-tau^2 / (2 s^2)), s = 1/(2 pi bw), on the
+        assembly's incident faces; its face integrals use a collapsed Gauss
+        rule with `quad` points per direction (default p + 4)."""
+        self.inc = dict(E0=np.asarray(E0, np.float64), d=np.asarray(direction, np.float64),
+                        c=float(speed), f0=float(f0), bw=float(bw), t0=float(t0),
+                        quad=int(quad) if quad else self.asm.p + 4)
+
+    def incident_vector(self, t):
+        """Forcing of the incident faces (e+ - e- = 2 E_inc, h+ = -h-, Z+ = Z-):
+        H rows -(phi, n x E_inc)_F (central and upwind alike), E rows
+        -(1/Z) (phi, n x (n x E_inc))_F for the upwind flux; by quadrature on
+        each face at physical points."""
+        from .basis import tri_quadrature
+        a, m = self.asm, self.asm.mesh
+        f = np.zeros((a.Kmat.shape[0], self.S))
+        inc = getattr(self, "inc", None)
+        if inc is None or not a.incident:
+            return f
+        st, wst = tri_quadrature(inc["quad"])
+        s = 1.0 / (2.0 * math.pi * inc["bw"])
+        Z = np.sqrt(a.mu / a.eps)
+        for (T, fc) in a.incident:
+            if a.pos[T] < 0:
+                continue
+            P, nrm, area = m.face_frame(T, fc)
+            r = P[0] + st[:, :1] * (P[1] - P[0]) + st[:, 1:2] * (P[2] - P[0])
+            w = wst * 2.0 * area
+            tau = t - inc["t0"] - r @ inc["d"] / inc["c"]
+            g = np.cos(2.0 * math.pi * inc["f0"] * tau) * np.exp(-tau ** 2 / (2.0 * s * s))
+            Einc = g[:, None] * inc["E0"][None, :]
+            B = a._basis_vectors(T, r)                                   # [q, 3, 3N]
+            nE = np.cross(nrm[None, :], Einc)
+            nnE = np.cross(nrm[None, :], nE)
+            r0 = a.pos[T] * a.n3
+            hoff = a.R * a.n3
+            f[hoff + r0:hoff + r0 + a.n3, :] -= np.einsum("q,qc,qci->i", w, nE, B)[:, None]
+            if a.flux == "upwind":
+                f[r0:r0 + a.n3, :] -= (np.einsum("q,qc,qci->i", w, nnE, B) / Z[T])[:, None]
+        return f
+
     def rhs(self, x, t=0.0):
         """du/dt for the assembled rows: M^-1 (K x + f(t))."""
         y = self.apply_k(x)
         if self.src:
             y = y + self.source_vector(t)
+        if getattr(self, "inc", None) is not None and self.asm.incident:
+            y = y + self.incident_vector(t)
         return self.asm.apply_minv(y)
 
     def lsrk4(self, x, t0, dt, steps, callback=None):
