@@ -369,6 +369,35 @@ int dgm_halo_unpack(dgm_plan* plan, void* fields, const int64_t* idx_device, int
  * the halo of the new current buffer.  Asynchronous. */
 int dgm_stage(dgm_plan* plan, int32_t k, double t);
 
+/* Incident plane wave (Sec. V, the PEC-sphere scattering set-up: a plane
+ * wave in a given direction with a smooth time envelope; Appendix A, the
+ * incidentfield boundary): E_inc(r, t) = E0 g(t - t0 - d . r / speed),
+ * g(x) = cos(2 pi f0 x) exp(-x^2 / (2 s^2)), s = 1 / (2 pi bw); f0 = 0 and
+ * s = w / sqrt(2) give the paper's exp(-((t - t0) / w)^2).  direction is used
+ * as given (pass a unit vector). */
+typedef struct {
+    double E0[3];         /* polarisation and amplitude */
+    double direction[3];  /* propagation direction d */
+    double speed;         /* phase speed (> 0) */
+    double f0, bw, t0;    /* carrier frequency, bandwidth (> 0), delay */
+} dgm_incident;
+
+/* Make n boundary faces (faces[n][3]: vertex ids, any order; host memory)
+ * incident faces: there the exterior state is e+ = e- + 2 E_inc, h+ = -h-
+ * with the element's own impedance (a magnetic wall that radiates the
+ * incident field into the mesh; the upwind flux absorbs what arrives from
+ * inside).  All columns see the same wave.  n = 0 restores PEC on every
+ * boundary face.  A later call replaces the previous set.  On a bound plan
+ * uploads the table and the neighbour codes (synchronises the stream).  The
+ * stage launches then evaluate the wave's face-mode integrals at each stage
+ * time (collapsed Gauss rule with (p + 6)^2 points per face, FP64).
+ * Errors: DGM_EINVAL (a face that is not a boundary face, given twice, bad
+ * wave parameters); DGM_EUNSUP on mixed-order and leapfrog plans.  A plan
+ * on a paired FP32 stage variant moves to variant 0; afterwards the paired
+ * variants are refused (dgm_set_variant) or skipped (dgm_autotune), and
+ * the adjoint and the batch refuse the plan. */
+int dgm_set_incident(dgm_plan* plan, int64_t n, const int64_t* faces, const dgm_incident* wave);
+
 /* Read and clear the device status word (synchronises).  Returns DGM_OK or
  * the latched device error. */
 int dgm_status_check(dgm_plan* plan);

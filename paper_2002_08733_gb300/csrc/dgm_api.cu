@@ -52,6 +52,10 @@ constexpr int ENERGY_THREADS = 256;
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// incident plane-wave table: header values, values per face, largest face rule
+constexpr int INC_HDR = 8, INC_FACE = 6, INC_MAXQ = 128;
+static_assert((PMAX + 6) * (PMAX + 6) <= INC_MAXQ, "face rule larger than a warp's four rounds");
+
 // Bytes of the tensor-core variant's operator image for degree p (0: no variant).
 static size_t tc_image_bytes(int p) {
     switch (p) {
@@ -156,6 +160,13 @@ struct dgm_plan {
     int tile_groups = 1;      // tile visiting order (dgm_autotune, dgm_set_tile_groups)
     int64_t k_active = 0;     // elements updated (dgm_set_active); the rest are halo copies
     float variant_ms[8] = {0};
+    // incident plane wave (dgm_set_incident)
+    int64_t n_bfaces = 0;     // boundary faces of the mesh: capacity of the incident tables
+    int64_t n_inc = 0;        // incident faces (codes -2 - i in the neighbour table)
+    int inc_nq = 0;           // points of the face rule
+    size_t off_inc = 0, off_incv = 0;
+    std::vector<double> inc_host;    // the FP64 table (layout at incident_eval)
+    std::vector<int32_t> nbr_plain;  // neighbour table without incident codes
 };
 
 static thread_local std::string g_err;
@@ -375,6 +386,17 @@ static int plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt
     P->bytes_ops = mixed ? (P->S.size() + P->R.size()) * size_t(kt->real_size) : 0;
     P->off_ops = off;
     off = align256(off + P->bytes_ops);
+    // incident plane wave: FP64 table and per-stage jump terms, sized for every boundary face
+    for (int64_t i = 0; i < 4 * K; ++i) P->n_bfaces += P->mesh.nbr[i] < 0;
+    P->inc_nq = (pE + 6) * (pE + 6);
+    P->off_inc = off;
+    if (!mixed) {
+        off = align256(off + sizeof(double) * (INC_HDR + size_t(P->inc_nq) * (2 + P->NF) +
+                                               size_t(INC_FACE) * P->n_bfaces));
+        P->off_incv = off;
+        off = align256(off + size_t(kt->real_size) * 3 * P->NF * P->n_bfaces);
+    }
+    P->nbr_plain = P->mesh.nbr;
     P->bytes_geom = off;
     P->k_active = K;
     P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
@@ -513,6 +535,10 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
                                  st)) != cudaSuccess)
             return cuda_fail(e, "upload mixed-order operators");
     }
+    if (P->n_inc > 0 &&
+        (e = cudaMemcpyAsync(P->geom + P->off_inc, P->inc_host.data(), sizeof(double) * P->inc_host.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "upload incident table");
     if (int rc = build_face_table(P)) return rc;
     // the host copies above are pageable: finish them before the host vectors can change
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
@@ -542,7 +568,80 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.tc_b = P->bytes_tcb ? static_cast<const void*>(P->geom + P->off_tcb) : nullptr;
     prm.K_active = P->k_active;
     prm.ops = P->bytes_ops ? static_cast<const void*>(P->geom + P->off_ops) : nullptr;
+    prm.inc = P->n_inc > 0 ? static_cast<const void*>(P->geom + P->off_incv) : nullptr;
 }
+
+}  // extern "C"
+
+// Incident plane-wave table (FP64, in the geometry buffer):
+//   [0, INC_HDR)  header: f0, bw, t0, nq, n_faces, 0, 0, 0
+//   then the face rule: (s_q, t_q) (2 nq values), W[m][q] = w_q psi_m(s_q, t_q)
+//       (NF nq values; the parametrisation of the trace operators)
+//   then per incident face i (INC_FACE values): A^T E0 (the polarisation's
+//       covariant components in the face's element), and tau_q = c0 + s_q cs + t_q ct,
+//       the plane-wave delay d . r_q / speed, linear on the face
+// incident_eval writes, for the stage time t, v[i][m][r] = 2 (A^T E0)_r s_m(t) with
+//   s_m(t) = sum_q W[m][q] g(t - t0 - tau_q),  g(x) = cos(2 pi f0 x) exp(-x^2 / (2 s^2)),
+//   s = 1 / (2 pi bw): the face-mode traces of the E jump 2 E_inc (e+ = e- + 2 E_inc).
+// One warp per face: the lanes take the rule's points, then reduce per mode.
+template <typename R>
+__global__ void incident_eval(const double* __restrict__ tab, int NF, double t, R* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nf = int64_t(tab[4]);
+    if (i >= nf) return;
+    const double twopi = 6.283185307179586476925286766559;
+    const double f0 = tab[0], sg = 1.0 / (twopi * tab[1]), t0 = tab[2];
+    const int nq = int(tab[3]);
+    const double* pts = tab + INC_HDR;
+    const double* W = pts + 2 * nq;
+    const double* fc = W + int64_t(NF) * nq + i * INC_FACE;
+    double g[INC_MAXQ / 32];
+#pragma unroll
+    for (int k = 0; k < INC_MAXQ / 32; ++k) {
+        const int q = lane + 32 * k;
+        g[k] = 0.0;
+        if (q < nq) {
+            const double x = t - t0 - (fc[3] + pts[2 * q] * fc[4] + pts[2 * q + 1] * fc[5]);
+            g[k] = cos(twopi * f0 * x) * exp(-x * x / (2.0 * sg * sg));
+        }
+    }
+    for (int m = 0; m < NF; ++m) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < INC_MAXQ / 32; ++k) {
+            const int q = lane + 32 * k;
+            if (q < nq) acc += W[int64_t(m) * nq + q] * g[k];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane < 3) out[(i * NF + m) * 3 + lane] = R(2.0 * fc[lane] * acc);
+    }
+}
+
+// A stage launch; with incident faces, their jump terms at the stage time first.
+static int launch_stage(dgm_plan* P, StageParams& prm, int mode, cudaStream_t st) {
+    if (P->n_inc > 0) {
+        const double* tab = reinterpret_cast<const double*>(P->geom + P->off_inc);
+        const unsigned grid = unsigned((P->n_inc + 3) / 4);
+        if (P->kt->real_size == 8)
+            incident_eval<double><<<grid, 128, 0, st>>>(tab, P->NF, prm.t,
+                                                         reinterpret_cast<double*>(P->geom + P->off_incv));
+        else
+            incident_eval<float><<<grid, 128, 0, st>>>(tab, P->NF, prm.t,
+                                                        reinterpret_cast<float*>(P->geom + P->off_incv));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return DGM_ECUDA;
+    }
+    return P->kt->launch_stage(prm, mode, st);
+}
+
+// The paired FP32 stage kernels (variants 3 and 4 up to p = 3) have no incident faces.
+static bool variant_has_incident(const dgm_plan* P, int v) {
+    return !(P->kt->real_size == 4 && P->opt.p <= 3 && (v == 3 || v == 4));
+}
+
+extern "C" {
 
 int dgm_set_sources(dgm_plan* P, int32_t n, const int32_t* column, const double* pos,
                     const double* dir, const double* f0, const double* bw, const double* t0) {
@@ -679,7 +778,7 @@ int dgm_rhs(dgm_plan* P, const void* fields, const void* aux, void* dfields, voi
     prm.aux = aux;
     prm.aux_out = daux;
     prm.t = t;
-    int rc = P->kt->launch_stage(prm, MODE_RHS, P->stream);
+    int rc = launch_stage(P, prm, MODE_RHS, P->stream);
     return rc ? fail(rc, "stage kernel launch failed") : DGM_OK;
 }
 
@@ -694,7 +793,7 @@ int dgm_leapfrog_start(dgm_plan* P, double t0) {
     prm.aux_out = P->aux[P->cur];
     prm.dt = 0.5 * P->opt.dt;
     prm.t = t0;
-    int rc = P->kt->launch_stage(prm, MODE_LF_H, P->stream);
+    int rc = launch_stage(P, prm, MODE_LF_H, P->stream);
     return rc ? fail(rc, "stage kernel launch failed") : DGM_OK;
 }
 
@@ -717,7 +816,7 @@ int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
                 prm.t = t + LSRK_C[k] * dt;
                 prm.a = LSRK_A[k];
                 prm.b = LSRK_B[k];
-                int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+                int rc = launch_stage(P, prm, MODE_LSRK, P->stream);
                 if (rc) return fail(rc, "stage kernel launch failed");
                 P->cur = 1 - P->cur;
             }
@@ -727,10 +826,10 @@ int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
             prm.aux = P->aux[P->cur];   // PML auxiliaries, updated in place
             prm.aux_out = P->aux[P->cur];
             prm.t = t + 0.5 * dt;
-            int rc = P->kt->launch_stage(prm, MODE_LF_E, P->stream);
+            int rc = launch_stage(P, prm, MODE_LF_E, P->stream);
             if (rc) return fail(rc, "stage kernel launch failed");
             prm.t = t + dt;
-            rc = P->kt->launch_stage(prm, MODE_LF_H, P->stream);
+            rc = launch_stage(P, prm, MODE_LF_H, P->stream);
             if (rc) return fail(rc, "stage kernel launch failed");
         }
     }
@@ -755,9 +854,108 @@ int dgm_stage(dgm_plan* P, int32_t k, double t) {
     prm.t = t + LSRK_C[k] * dt;
     prm.a = LSRK_A[k];
     prm.b = LSRK_B[k];
-    int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+    int rc = launch_stage(P, prm, MODE_LSRK, P->stream);
     if (rc) return fail(rc, "stage kernel launch failed");
     P->cur = 1 - P->cur;
+    return DGM_OK;
+}
+
+int dgm_set_incident(dgm_plan* P, int64_t n, const int64_t* faces, const dgm_incident* w) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (n < 0) return fail(DGM_EINVAL, "negative face count");
+    if (n > 0 && (!faces || !w)) return fail(DGM_EINVAL, "null faces or wave");
+    if (n > 0 && P->mixed) return fail(DGM_EUNSUP, "mixed-order plans have no incident faces");
+    if (n > 0 && P->opt.integrator != DGM_LSRK4) return fail(DGM_EUNSUP, "incident faces need LSRK4");
+    if (n > P->n_bfaces) return fail(DGM_EINVAL, "more incident faces than boundary faces");
+    const int64_t K = P->mesh.K;
+    std::vector<int32_t> nbr = P->nbr_plain;
+    std::vector<double> tab;
+    if (n > 0) {
+        bool ok = w->bw > 0.0 && w->speed > 0.0 && std::isfinite(w->bw) && std::isfinite(w->speed) &&
+                  std::isfinite(w->f0) && std::isfinite(w->t0);
+        for (int c = 0; c < 3; ++c) ok = ok && std::isfinite(w->E0[c]) && std::isfinite(w->direction[c]);
+        if (!ok) return fail(DGM_EINVAL, "invalid incident wave parameters");
+        // boundary faces by sorted vertex triple
+        struct Key {
+            int64_t a, b, c, id;
+            bool operator<(const Key& o) const {
+                return a != o.a ? a < o.a : b != o.b ? b < o.b : c != o.c ? c < o.c : id < o.id;
+            }
+        };
+        std::vector<Key> bf;
+        bf.reserve(size_t(P->n_bfaces));
+        for (int64_t e = 0; e < K; ++e)
+            for (int f = 0; f < 4; ++f) {
+                if (P->nbr_plain[size_t(f) * K + e] >= 0) continue;
+                int64_t t[3], c = 0;
+                for (int i = 0; i < 4; ++i)
+                    if (i != f) t[c++] = P->mesh.vid[4 * e + i];
+                bf.push_back(Key{t[0], t[1], t[2], 4 * e + f});
+            }
+        std::sort(bf.begin(), bf.end());
+        const int q1 = P->pE + 6;
+        std::vector<double> pts, wq, psi;
+        face_rule(P->pE, q1, pts, wq, psi);
+        const int nq = int(wq.size()), NF = P->NF;
+        tab.assign(INC_HDR + size_t(nq) * (2 + NF) + size_t(INC_FACE) * n, 0.0);
+        tab[0] = w->f0;
+        tab[1] = w->bw;
+        tab[2] = w->t0;
+        tab[3] = nq;
+        tab[4] = double(n);
+        for (int q = 0; q < nq; ++q) {
+            tab[INC_HDR + 2 * q] = pts[2 * q];
+            tab[INC_HDR + 2 * q + 1] = pts[2 * q + 1];
+            for (int m = 0; m < NF; ++m) tab[INC_HDR + 2 * nq + size_t(m) * nq + q] = wq[q] * psi[size_t(q) * NF + m];
+        }
+        double* fc = tab.data() + INC_HDR + size_t(nq) * (2 + NF);
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t v[3] = {faces[3 * i], faces[3 * i + 1], faces[3 * i + 2]};
+            std::sort(v, v + 3);
+            const Key k{v[0], v[1], v[2], -1};
+            auto it = std::lower_bound(bf.begin(), bf.end(), k);
+            if (it == bf.end() || it->a != v[0] || it->b != v[1] || it->c != v[2])
+                return fail(DGM_EINVAL, "incident face " + std::to_string(i) + " is not a boundary face");
+            const int64_t e = it->id / 4;
+            const int f = int(it->id % 4);
+            if (nbr[size_t(f) * K + e] != P->nbr_plain[size_t(f) * K + e])
+                return fail(DGM_EINVAL, "incident face " + std::to_string(i) + " given twice");
+            nbr[size_t(f) * K + e] = int32_t(-2 - i);
+            const double* X = P->mesh.verts.data() + 12 * e;   // sorted local vertices
+            int loc[3], c = 0;
+            for (int j = 0; j < 4; ++j)
+                if (j != f) loc[c++] = j;
+            for (int j = 0; j < 3; ++j) {   // (A^T E0)_j = (X_{j+1} - X_0) . E0
+                double acc = 0.0;
+                for (int r = 0; r < 3; ++r) acc += (X[3 * (j + 1) + r] - X[r]) * w->E0[r];
+                fc[INC_FACE * i + j] = acc;
+            }
+            double dpa = 0.0, dpb = 0.0, dpc = 0.0;   // d . P_a, d . (P_b - P_a), d . (P_c - P_a)
+            for (int r = 0; r < 3; ++r) {
+                const double pa = X[3 * loc[0] + r];
+                dpa += w->direction[r] * pa;
+                dpb += w->direction[r] * (X[3 * loc[1] + r] - pa);
+                dpc += w->direction[r] * (X[3 * loc[2] + r] - pa);
+            }
+            fc[INC_FACE * i + 3] = dpa / w->speed;
+            fc[INC_FACE * i + 4] = dpb / w->speed;
+            fc[INC_FACE * i + 5] = dpc / w->speed;
+        }
+    }
+    P->mesh.nbr = nbr;
+    P->inc_host = tab;
+    P->n_inc = n;
+    if (n > 0 && !variant_has_incident(P, P->variant)) P->variant = 0;
+    if (P->bound) {
+        cudaStream_t st = P->stream;
+        cudaError_t e = cudaMemcpyAsync(P->geom + P->off_nbr, P->mesh.nbr.data(), sizeof(int32_t) * 4 * K,
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(P->geom + P->off_inc, P->inc_host.data(), sizeof(double) * P->inc_host.size(),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "upload incident faces");
+    }
     return DGM_OK;
 }
 
@@ -1077,6 +1275,7 @@ extern "C" int dgm_batch_create(dgm_batch** out, dgm_plan* const* members, int32
         if (members[i]->k_active < members[i]->mesh.K)
             return fail(DGM_EINVAL, "batch members must have every element active (no halo)");
         if (members[i]->mixed) return fail(DGM_EUNSUP, "mixed-order plans are not batched");
+        if (members[i]->n_inc > 0) return fail(DGM_EUNSUP, "plans with incident faces are not batched");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(DGM_EINVAL, "duplicate batch member");
     }
@@ -1292,6 +1491,7 @@ static int copy_state(dgm_plan* P, StateRef dst, const void* f, const void* a, c
 extern "C" int dgm_forward_record(dgm_plan* P, int64_t n_steps, double t0, double* records, void* ws_) {
     if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
     if (P && P->mixed) return fail(DGM_EUNSUP, "the adjoint is not built for mixed-order plans");
+    if (P && P->n_inc > 0) return fail(DGM_EUNSUP, "the adjoint is not built for incident faces");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (P->opt.integrator != DGM_LSRK4) return fail(DGM_EUNSUP, "the adjoint needs LSRK4");
     if (!records || !ws_ || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
@@ -1358,6 +1558,7 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
                            double* deps, double* dmu) {
     if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
     if (P && P->mixed) return fail(DGM_EUNSUP, "the adjoint is not built for mixed-order plans");
+    if (P && P->n_inc > 0) return fail(DGM_EUNSUP, "the adjoint is not built for incident faces");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (!drec || !ws_ || !deps || !dmu || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
     if (reinterpret_cast<uintptr_t>(ws_) % 256) return fail(DGM_EINVAL, "workspace must be 256-byte aligned");
@@ -1492,7 +1693,7 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
         prm.aux_out = abuf[0];
         prm.a = 0.0;
         prm.b = LSRK_B[0];
-        int rc = P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+        int rc = launch_stage(P, prm, MODE_LSRK, P->stream);
         if (rc) return fail(rc, "stage kernel launch failed");
         int src = 0;   // buffer holding the last output
         cudaEventRecord(e0, P->stream);
@@ -1507,7 +1708,7 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
                 prm.b = LSRK_B[k];
                 src = 1 - src;
             }
-            P->kt->launch_stage(prm, MODE_LSRK, P->stream);
+            launch_stage(P, prm, MODE_LSRK, P->stream);
         }
         cudaEventRecord(e1, P->stream);
         cudaError_t e = cudaEventSynchronize(e1);
@@ -1520,6 +1721,10 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
     float best_ms = 1e30f;
     prm.tile_groups = 1;
     for (int v = 0; v < P->kt->n_variants && rc == DGM_OK; ++v) {
+        if (P->n_inc > 0 && !variant_has_incident(P, v)) {
+            if (ms_out) ms_out[v] = 0.f;
+            continue;
+        }
         prm.variant = v;
         float ms = 0.f;
         if ((rc = time_it(reps, &ms)) != DGM_OK) break;
@@ -1579,6 +1784,8 @@ extern "C" int dgm_autotune_info(const dgm_plan* P, int32_t* n_variants, int32_t
 extern "C" int dgm_set_variant(dgm_plan* P, int32_t v) {
     if (!P) return fail(DGM_EINVAL, "null plan");
     if (v < 0 || v >= P->kt->n_variants) return fail(DGM_EINVAL, "variant out of range");
+    if (P->n_inc > 0 && !variant_has_incident(P, v))
+        return fail(DGM_EUNSUP, "the paired stage variants have no incident faces");
     P->variant = v;
     return DGM_OK;
 }

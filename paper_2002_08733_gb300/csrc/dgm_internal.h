@@ -109,6 +109,8 @@ struct StageParams {
     const void* tc_b;     // tensor-core variant: B operand image (TcShape<P>::B_BYTES), or null
     int64_t K_active;     // elements updated: the first K_active (the rest are halo copies)
     const void* ops;      // mixed-order plans: dense reference operators S, R of degree p + 1
+    const void* inc;      // incident faces: [i][NF][3] reference-frame jump terms
+                          // 2 A^T E_inc traced on face mode m at the stage time (R), or null
 };
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms
@@ -157,6 +159,7 @@ struct HostMesh {
     std::vector<int32_t> nbr;         // 4 * K
     std::vector<int32_t> pml_idx;     // K
     std::vector<double> verts;        // K * 12 (sorted local vertices)
+    std::vector<int64_t> vid;         // K * 4 (sorted vertex ids)
     int64_t npml = 0;
 };
 
@@ -173,5 +176,11 @@ void ref_basis_values(int p, const double xr[3], double* out);
 
 // Collapsed Gauss-Legendre rule on the reference tetrahedron.
 void tet_rule(int q, std::vector<double>& pts, std::vector<double>& w);
+
+// Collapsed Gauss-Legendre rule on the reference triangle {s, t >= 0, s + t <= 1}
+// (q points per direction: pts [n][2], w [n]) and the orthonormal face basis of
+// degree p at its points (psi [n][NF]); the parametrisation of the trace operators.
+void face_rule(int p, int q, std::vector<double>& pts, std::vector<double>& w,
+               std::vector<double>& psi);
 
 }  // namespace dgm

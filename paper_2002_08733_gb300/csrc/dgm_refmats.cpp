@@ -177,6 +177,14 @@ void tet_rule(int q, std::vector<double>& pts, std::vector<double>& w) {
             }
 }
 
+void face_rule(int p, int q, std::vector<double>& pts, std::vector<double>& w,
+               std::vector<double>& psi) {
+    tri_rule(q, pts, w);
+    const int NF = nfmodes(p);
+    psi.assign(w.size() * NF, 0.0);
+    for (size_t i = 0; i < w.size(); ++i) face_basis(p, pts[2 * i], pts[2 * i + 1], &psi[i * NF]);
+}
+
 void ref_basis_values(int p, const double xr[3], double* out) {
     Dual d[nmodes(PMAX)];
     basis_dual(p, xr, d);

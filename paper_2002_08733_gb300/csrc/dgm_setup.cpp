@@ -42,6 +42,7 @@ int build_mesh(int64_t nv, const double* xyz, int64_t nt, const int64_t* tets, c
     out.nbr.assign(size_t(4) * K, -1);
     out.pml_idx.assign(size_t(K), -1);
     out.verts.assign(size_t(12) * K, 0.0);
+    out.vid.assign(size_t(4) * K, 0);
     std::vector<std::array<int64_t, 4>> sv(K);
     for (int64_t e = 0; e < K; ++e) {
         std::array<int64_t, 4> v;
@@ -59,6 +60,7 @@ int build_mesh(int64_t nv, const double* xyz, int64_t nt, const int64_t* tets, c
                 return DGM_EMESH;
             }
         sv[e] = v;
+        for (int i = 0; i < 4; ++i) out.vid[4 * e + i] = v[i];
         if (!(eps[e] > 0.0) || !(mu[e] > 0.0) || !std::isfinite(eps[e]) || !std::isfinite(mu[e])) {
             err = "eps and mu must be positive and finite (element " + std::to_string(e) + ")";
             return DGM_EINVAL;

@@ -83,7 +83,8 @@ constexpr int FGR = 15;
 enum FaceConstRef {
     FR_Q = 0,     // Q = A^T A_n^-T (9, row major): neighbour reference components -> own
     FR_NAE = 9,   // -alpha_E: -1 on an interior face, -2 on a PEC face (e+ = -e-)
-    FR_NAH = 10,  // -alpha_H: -1 on an interior face, 0 on a PEC face (h+ = h-)
+    FR_NAH = 10,  // -alpha_H: -1 on an interior face, 0 on a PEC face (h+ = h-),
+                  // -2 on an incident face (h+ = -h-; there alpha_E = 0)
     FR_CE = 11,   // s_T c_E
     FR_BE = 12,   // b_E / (|det A| |A^-T m_f|)
     FR_CH = 13,   // s_T c_H
@@ -188,10 +189,12 @@ __device__ __forceinline__ void face_constants_tab(int f, const R (&ait)[9], R d
 // faces x = 0, y = 0, z = 0 (m_f = -e_a) the cross products only permute
 // components, component a of g vanishes, and component a of the own trace
 // is not needed.
+// incident: a boundary face through which an incident field enters (ghost state
+// e+ = e- + 2 E_inc, h+ = -h-, Z+ = Z-; the E_inc part is added by flux_face).
 template <typename R, int TE>
 __device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R det, R epsm, R mum,
                                                    bool has_nbr, const R (&aitn)[9], R zn,
-                                                   int upwind, R* fc, R* gm) {
+                                                   int upwind, R* fc, R* gm, bool incident = false) {
     // A^T = det A adj(A^-T), row major
     R at[9];
     at[0] = ait[4] * ait[8] - ait[5] * ait[7];
@@ -230,8 +233,8 @@ __device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R d
         ch = yp / (ym + yp);
         bh = R(1) / (ym + yp);
     }
-    fc[FR_NAE * TE] = has_nbr ? R(-1) : R(-2);
-    fc[FR_NAH * TE] = has_nbr ? R(-1) : R(0);
+    fc[FR_NAE * TE] = has_nbr ? R(-1) : (incident ? R(0) : R(-2));
+    fc[FR_NAH * TE] = has_nbr ? R(-1) : (incident ? R(-2) : R(0));
     fc[FR_CE * TE] = st * ce;
     fc[FR_BE * TE] = kb * be;
     fc[FR_CH * TE] = st * ch;
@@ -259,7 +262,8 @@ __host__ __device__ constexpr int sym3(int i, int j) {
 template <int F, int NF, typename R, int TE, int MODE, typename IX>
 __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R* trN,
                                           const R* fg, const R* gm, const R* eg, R* jumps,
-                                          IX C, IX col, bool active) {
+                                          IX C, IX col, bool active, int32_t code = -1,
+                                          const StageParams* prm = nullptr) {
     constexpr bool DO_E = (MODE != MODE_LF_H);   // E fluxes needed
     constexpr bool DO_H = (MODE != MODE_LF_E);   // H fluxes needed
     constexpr bool HAS_E = (MODE != MODE_LF_E);  // E jump used (H flux, upwind E flux)
@@ -289,6 +293,10 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
     const R gcb = gsym(CC, B), gcc = gsym(CC, CC), gbb = gsym(B, B);
     const R kEcb = bE * gcb, kEcc = bE * gcc, kEbb = bE * gbb;
     const R kHcb = bH * gcb, kHcc = bH * gcc, kHbb = bH * gbb;
+    // incident face (e+ = e- + 2 E_inc): the E jump is the incident term alone
+    const R* inc = (HAS_E && code <= -2 && prm != nullptr && prm->inc != nullptr && active)
+                       ? static_cast<const R*>(prm->inc) + IX(-code - 2) * NF * 3
+                       : nullptr;
     // not unrolled: four copies of an unrolled loop (one per face) cost more in
     // instruction fetch than the loop overhead they save
 #pragma unroll 1
@@ -305,6 +313,11 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
                 if (FULL || r != A)
                     de[r] = q[3 * r] * tp[0] + q[3 * r + 1] * tp[1] + q[3 * r + 2] * tp[2] +
                             nae * own[r * NF * TE];
+        }
+        if (inc != nullptr) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                if (FULL || r != A) de[r] += inc[m * 3 + r];
         }
         if (HAS_H) {
             R tp[3];
@@ -510,7 +523,8 @@ stage_kernel(const StageParams prm) {
         const R mum = active ? gr[IX(G_MU) * K + e] : R(1);
         const R zn = active ? fn[IX(FNB_Z) * K] : R(1);
         face_constants_ref<R, TE>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
-                                  prm.upwind, fg + f * FGR * TE + c, f == 0 ? gm + c : nullptr);
+                                  prm.upwind, fg + f * FGR * TE + c, f == 0 ? gm + c : nullptr,
+                                  code <= -2 && prm.inc != nullptr);
     };
     // neighbour code of this group's round-0 item, loaded with the other
     // independent loads so that the dependent gather starts one round trip in
@@ -624,7 +638,10 @@ stage_kernel(const StageParams prm) {
 
     // ---- phase 3: numerical flux per (face, chunk of face modes) -------------
     // in the element's reference frame, one code path per face (the face of an
-    // item is uniform over its warp-sized group)
+    // item is uniform over its warp-sized group).  Equal chunks per face,
+    // although a mode of the slanted face 0 costs more than one of an axis face
+    // (66 against 28 operations): chunks sized by that ratio measured slower
+    // (more items, so more per-item setup, and no shorter phase).
     {
         constexpr int CHUNKS = NG >= 12 ? (NG / 4) : (NG == 8 ? 2 : 1);   // face-mode chunks per face
         R* jp = static_cast<R*>(prm.jumps);
@@ -632,11 +649,12 @@ stage_kernel(const StageParams prm) {
             const int f = it / CHUNKS;
             const int ch = it % CHUNKS;
             const int m0 = ch * NF / CHUNKS, m1 = (ch + 1) * NF / CHUNKS;
+            const int32_t fcode = nbs[f * TE + c];
             switch (f) {
-                case 0: flux_face<0, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
-                case 1: flux_face<1, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
-                case 2: flux_face<2, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
-                default: flux_face<3, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active); break;
+                case 0: flux_face<0, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
+                case 1: flux_face<1, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
+                case 2: flux_face<2, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
+                default: flux_face<3, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
             }
         }
     }

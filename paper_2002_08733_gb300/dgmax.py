@@ -47,6 +47,12 @@ class HaloSizes(ctypes.Structure):
                 ("n_peers", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Incident(ctypes.Structure):
+    _fields_ = [("E0", ctypes.c_double * 3), ("direction", ctypes.c_double * 3),
+                ("speed", ctypes.c_double), ("f0", ctypes.c_double), ("bw", ctypes.c_double),
+                ("t0", ctypes.c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int64), ("n_pml", ctypes.c_int64), ("N", ctypes.c_int32),
                 ("NF", ctypes.c_int32), ("S", ctypes.c_int32), ("real_size", ctypes.c_int32),
@@ -100,6 +106,7 @@ _SIGS = {
     "dgm_halo_pack": [_P, _P, _P, ctypes.c_int64, _P],
     "dgm_halo_unpack": [_P, _P, _P, ctypes.c_int64, _P],
     "dgm_stage": [_P, ctypes.c_int32, ctypes.c_double],
+    "dgm_set_incident": [_P, ctypes.c_int64, _P, ctypes.POINTER(Incident)],
     "dgm_last_error": [],
     "dgm_plan_destroy": [_P],
 }
@@ -195,6 +202,17 @@ class Plan:
         out = np.empty((self.K, self.info.n_quad, 3))
         _check(_lib.dgm_quad_points(self.handle, out.ctypes.data))
         return out
+
+    def set_incident(self, faces, E0=(0.0, 0.0, 0.0), direction=(0.0, 0.0, 1.0), speed=1.0,
+                     f0=0.0, bw=1.0, t0=0.0):
+        """Incident plane wave E0 g(t - t0 - d.r/speed) entering through the
+        boundary faces `faces` [n, 3] (vertex ids); an empty list restores PEC."""
+        f = np.ascontiguousarray(np.asarray(faces, dtype=np.int64).reshape(-1, 3))
+        w = Incident((ctypes.c_double * 3)(*map(float, E0)),
+                     (ctypes.c_double * 3)(*map(float, direction)),
+                     float(speed), float(f0), float(bw), float(t0))
+        _check(_lib.dgm_set_incident(self.handle, len(f), f.ctypes.data if len(f) else None,
+                                     ctypes.byref(w)))
 
 
 class Solver(Plan):

@@ -180,3 +180,40 @@ def test_mixed_order_plan_sizes_and_limits(lib):
         with pytest.raises(D.DgmError):
             D.Plan(xyz, tets, 1.0, 1.0, args["p"], args["precision"], args["flux"],
                    args["integrator"], args["dt"], mixed=True, **extra)
+
+
+def test_incident_faces_are_validated_on_the_host(lib):
+    """dgm_set_incident: boundary faces only, each once, a positive bandwidth
+    and speed; refused on mixed-order and leapfrog plans; the paired FP32
+    variants are refused while incident faces are set.  No CUDA call."""
+    from paper_2002_08733_gb300 import dgmax as D
+    xyz, tets = W.kuhn_mesh(2)
+    on_z0 = lambda tri: np.all(np.abs(xyz[list(tri), 2]) < 1e-12)
+    bnd, inner = [], []
+    from oracle.mesh import Mesh          # face adjacency for choosing the test faces
+    m = Mesh(xyz, tets)
+    for T in range(m.K):
+        for f in range(4):
+            tri = np.delete(m.tets[T], f)
+            (bnd if m.nbr[T, f] < 0 else inner).append(tri)
+    z0 = [t for t in bnd if on_z0(t)]
+    assert len(z0) == 8
+    wave = dict(E0=(1, 0, 0), direction=(0, 0, 1), speed=1.0, f0=0.0, bw=1.0, t0=0.3)
+    pl = D.Plan(xyz, tets, 1.0, 1.0, 3, "fp32", "upwind", "lsrk4", 1e-3)
+    pl.set_incident([t[::-1] for t in z0], **wave)          # any vertex order
+    for bad in ([inner[0]], [z0[0], z0[0]], [[0, 1, 10 ** 6]]):
+        with pytest.raises(D.DgmError):
+            pl.set_incident(bad, **wave)
+    for kw in (dict(bw=0.0), dict(speed=-1.0), dict(t0=float("nan"))):
+        with pytest.raises(D.DgmError):
+            pl.set_incident(z0, **{**wave, **kw})
+    pl.set_incident(z0, **wave)
+    for v in (3, 4):
+        assert D.STATUS[lib.dgm_set_variant(pl.handle, v)] == "DGM_EUNSUP"
+    assert lib.dgm_set_variant(pl.handle, 0) == 0
+    pl.set_incident([], **wave)                              # back to PEC everywhere
+    assert lib.dgm_set_variant(pl.handle, 3) == 0
+    for plan in (D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", "upwind", "lsrk4", 1e-3, mixed=True),
+                 D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", "central", "leapfrog", 1e-3)):
+        with pytest.raises(D.DgmError):
+            plan.set_incident(z0, **wave)

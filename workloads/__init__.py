@@ -89,6 +89,23 @@ def kuhn_mesh(n: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), jitter: float = 0.
     return xyz, tets.reshape(-1, 4)
 
 
+def box_faces(n, tets, axis, side):
+    """Faces of a kuhn_mesh(n, ...) grid on one side of the box (side 0: the
+    `lo` plane, 1: the `hi` plane of `axis`), as vertex-id triples: the faces
+    whose three vertices have grid index 0 (or n) along `axis`.  Topology
+    only; jitter does not move boundary vertices.  2 n^2 faces."""
+    m = n + 1
+    tets = np.asarray(tets, dtype=np.int64)
+    grid = [tets % m, (tets // m) % m, tets // (m * m)][axis]
+    on = grid == (0 if side == 0 else n)
+    out = []
+    for f in range(4):
+        keep = [v for v in range(4) if v != f]
+        sel = np.all(on[:, keep], axis=1)
+        out.extend(tets[sel][:, keep].tolist())
+    return np.asarray(out, dtype=np.int64).reshape(-1, 3)
+
+
 def centroids(xyz, tets):
     """Arithmetic mean of each tetrahedron's four vertices."""
     return xyz[tets].mean(axis=1)
