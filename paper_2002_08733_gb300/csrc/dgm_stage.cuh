@@ -263,7 +263,7 @@ template <int F, int NF, typename R, int TE, int MODE, typename IX>
 __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R* trN,
                                           const R* fg, const R* gm, const R* eg, R* jumps,
                                           IX C, IX col, bool active, int32_t code = -1,
-                                          const StageParams* prm = nullptr) {
+                                          const void* incp = nullptr) {
     constexpr bool DO_E = (MODE != MODE_LF_H);   // E fluxes needed
     constexpr bool DO_H = (MODE != MODE_LF_E);   // H fluxes needed
     constexpr bool HAS_E = (MODE != MODE_LF_E);  // E jump used (H flux, upwind E flux)
@@ -294,8 +294,8 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
     const R kEcb = bE * gcb, kEcc = bE * gcc, kEbb = bE * gbb;
     const R kHcb = bH * gcb, kHcc = bH * gcc, kHbb = bH * gbb;
     // incident face (e+ = e- + 2 E_inc): the E jump is the incident term alone
-    const R* inc = (HAS_E && code <= -2 && prm != nullptr && prm->inc != nullptr && active)
-                       ? static_cast<const R*>(prm->inc) + IX(-code - 2) * NF * 3
+    const R* inc = (HAS_E && code <= -2 && incp != nullptr && active)
+                       ? static_cast<const R*>(incp) + IX(-code - 2) * NF * 3
                        : nullptr;
     // not unrolled: four copies of an unrolled loop (one per face) cost more in
     // instruction fetch than the loop overhead they save
@@ -392,18 +392,20 @@ __device__ __forceinline__ void rhs_rows(int comp, int c, const R* us, const R* 
     const R* g = trO + comp * NF * TE + c;    // face f of this component: g + f * 6 * NF * TE
     switch (j) {
         case 0:
-            DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 2) * N * TE, TE, sg, acc);
-            DerivOp<P, 2>::template apply<R, LO, HI>(base + (srcf + 1) * N * TE, TE, -sg, acc);
+            DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 2) * N * TE, TE, R(1), acc);
+            DerivOp<P, 2>::template apply<R, LO, HI>(base + (srcf + 1) * N * TE, TE, R(-1), acc);
             break;
         case 1:
-            DerivOp<P, 2>::template apply<R, LO, HI>(base + (srcf + 0) * N * TE, TE, sg, acc);
-            DerivOp<P, 0>::template apply<R, LO, HI>(base + (srcf + 2) * N * TE, TE, -sg, acc);
+            DerivOp<P, 2>::template apply<R, LO, HI>(base + (srcf + 0) * N * TE, TE, R(1), acc);
+            DerivOp<P, 0>::template apply<R, LO, HI>(base + (srcf + 2) * N * TE, TE, R(-1), acc);
             break;
         default:
-            DerivOp<P, 0>::template apply<R, LO, HI>(base + (srcf + 1) * N * TE, TE, sg, acc);
-            DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 0) * N * TE, TE, -sg, acc);
+            DerivOp<P, 0>::template apply<R, LO, HI>(base + (srcf + 1) * N * TE, TE, R(1), acc);
+            DerivOp<P, 1>::template apply<R, LO, HI>(base + (srcf + 0) * N * TE, TE, R(-1), acc);
             break;
     }
+#pragma unroll
+    for (int l = LO; l < HI; ++l) acc[l] *= sg;
     // one copy of each lift, skipped by a branch that is uniform over the
     // group (lifts inside the cases above would triple the code of this phase)
     LiftOp<P, 0>::template apply<R, LO, HI>(g + 0 * 6 * NF * TE, TE, acc);
@@ -651,10 +653,10 @@ stage_kernel(const StageParams prm) {
             const int m0 = ch * NF / CHUNKS, m1 = (ch + 1) * NF / CHUNKS;
             const int32_t fcode = nbs[f * TE + c];
             switch (f) {
-                case 0: flux_face<0, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
-                case 1: flux_face<1, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
-                case 2: flux_face<2, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
-                default: flux_face<3, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, &prm); break;
+                case 0: flux_face<0, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
+                case 1: flux_face<1, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
+                case 2: flux_face<2, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
+                default: flux_face<3, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
             }
         }
     }
