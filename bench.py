@@ -425,6 +425,62 @@ def run_mixed(precision, steps, warmup, n=32, p=2):
                 ms_per_step=ms / steps, value=dofs * steps / (ms * 1e-3))
 
 
+def run_boundary_and_penalty(steps, warmup, n=32, alpha=10.0):
+    """The incident-field boundary and the interior penalty on the jittered-sphere
+    mesh (p = 3, FP32, autotuned): time per LSRK4 step with incident faces on the
+    z = 0 side (upwind) against the same plan without them, and with the facet
+    field of the penalty (central flux) against the plain central flux.  The
+    penalty's algorithmic bytes add, per stage and facet, the facet field read by
+    both sides, the owner's residual read and write and its output write."""
+    import torch
+    from paper_2002_08733_gb300 import dgmax as D
+    w = W.jittered_sphere(n=n)
+    xyz, tets, eps = build_problem(w)
+    dev = torch.device("cuda", 0)
+    faces = W.box_faces(n, tets, 2, 0)
+
+    def timed(flux, incident=False, sip=None):
+        g = D.Solver(xyz, tets, eps, 1.0, w.p, "fp32", flux, "lsrk4", w.dt, device=dev, sip=sip)
+        g.project(pulse(w.extra["r0"]))
+        if incident:
+            g.set_incident(faces, E0=(1.0, 0.0, 0.0), direction=(0.0, 0.0, 1.0), speed=0.5,
+                           f0=2.0, bw=1.0, t0=0.5)
+        v, _ = g.autotune()
+        t = 0.0
+        for _ in range(warmup):
+            g.advance(1, t)
+            t += w.dt
+        torch.cuda.synchronize(dev)
+        st = torch.cuda.current_stream(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.advance(steps, t)
+        e1.record(st)
+        e1.synchronize()
+        g.status()
+        return e0.elapsed_time(e1) / steps, g, v
+
+    out = {"workload": "jittered sphere, %d^3 (%d tets), p=3, FP32, LSRK4, %d steps each" % (n, w.K, steps)}
+    ms0, g0, v0 = timed("upwind")
+    ms1, g1, v1 = timed("upwind", incident=True)
+    out["incident"] = dict(faces=int(len(faces)), ms_per_step=ms1, plain_ms_per_step=ms0,
+                           overhead=ms1 / ms0 - 1.0, variant=int(v1))
+    ms2, g2, v2 = timed("central")
+    ms3, g3, v3 = timed("central", sip=alpha)
+    nF = int(g3.info.n_facets)
+    base = stage_bytes(g3.K, g3.N, g3.S, 4)
+    unit = nF * g3.S * 3 * W.n_face_modes(w.p) * 4     # one facet-field buffer, FP32
+    facet = (5 * 5 - 1) * unit                          # five per stage, no residual read in the first
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out["sip"] = dict(alpha=alpha, facets=nF, ms_per_step=ms3, plain_central_ms_per_step=ms2,
+                      overhead=ms3 / ms2 - 1.0, variant=int(v3),
+                      bytes_per_step=base + facet,
+                      hbm_frac=(base + facet) / (ms3 * 1e-3) / (hbm * 1e9))
+    return out
+
+
 def fp64_reference_rate(n=8192, reps=5):
     """FP64 throughput reference of this GPU: cuBLAS DGEMM through torch.matmul
     (2 n^3 flop per product, best of `reps` after a warm-up), CUDA events."""
@@ -688,7 +744,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=32,
                     help="Kuhn grid size (32 = the benchmarked workload; smaller for profiling)")
-    ap.add_argument("--only", choices=["fp32", "fp64", "adjoint", "pml", "mixed"], default=None,
+    ap.add_argument("--only", choices=["fp32", "fp64", "adjoint", "pml", "mixed", "boundary"],
+                    default=None,
                     help="profile one precision (or the inverse-problem or dipole-in-PML leg) only")
     ap.add_argument("--pml-n", type=int, default=40,
                     help="Kuhn grid size of the dipole-in-PML leg (40 = the benchmarked workload)")
@@ -709,6 +766,9 @@ def main():
     ap.add_argument("--pml-steps", type=int, default=20)
     ap.add_argument("--mixed-steps", type=int, default=10)
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-order leg")
+    ap.add_argument("--no-boundary", action="store_true",
+                    help="skip the incident-boundary and interior-penalty leg")
+    ap.add_argument("--boundary-steps", type=int, default=200)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -761,6 +821,11 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
+    if args.only == "boundary":
+        r = run_boundary_and_penalty(args.boundary_steps, 3, n=args.n)
+        if rank == 0:
+            print(json.dumps({"profile_run": "boundary", **r}))
+        return
     if args.only == "mixed":
         r = [run_mixed(pr, args.mixed_steps, args.warmup, n=args.n) for pr in ("fp32", "fp64")]
         if rank == 0:
@@ -853,6 +918,8 @@ def main():
                      "kernel with dense operators" % (args.n, w.K),
             fp32=run_mixed("fp32", args.mixed_steps, 2, n=args.n),
             fp64=run_mixed("fp64", min(args.mixed_steps, 3), 1, n=args.n))
+    if not args.no_boundary and world == 1:
+        line["boundary_and_penalty"] = run_boundary_and_penalty(args.boundary_steps, 3, n=args.n)
     if world == 1:
         line["cavity"] = dict(workload="PEC cavity 4^3 (384 tets), p=2, central, leapfrog, "
                                        "TM110, 200 steps (latency regime, state fits in L2)",

@@ -98,6 +98,8 @@ typedef struct {
     size_t bytes_geom;    /* geometry + workspace buffer, 256-byte aligned start */
     int32_t n_quad;       /* projection quadrature points per element */
     int32_t N_H;          /* modes per H component: N, except on a mixed-order plan */
+    int64_t n_facets;     /* interior facets carrying the penalty's facet field (0: off) */
+    size_t bytes_facets;  /* one facet-field buffer: n_facets * S * 3 * NF reals */
 } dgm_info;
 
 /* Create a plan: validates the mesh, sorts each element's vertices, builds the
@@ -397,6 +399,29 @@ typedef struct {
  * variants are refused (dgm_set_variant) or skipped (dgm_autotune), and
  * the adjoint and the batch refuse the plan. */
 int dgm_set_incident(dgm_plan* plan, int64_t n, const int64_t* faces, const dgm_incident* wave);
+
+/* Symmetric interior penalty with a facet field (Sec. III, Eqs. (jmp_var_def),
+ * (1st_weak_equation), (weak_penalty), in the skew matrix form printed after
+ * them): every interior facet F carries a tangential field h_s of degree p,
+ *   E equation of both sides:  (eps de/dt, phi)_T += -(h_s x n_T, phi)_F
+ *   facet field:  (mu_F / alpha) (dh_s/dt, psi)_F = (n- x (e- - e+), psi)_F
+ * with T- the side of lower element index (its outward normal n-) and mu_F
+ * the mean of both sides' mu; alpha > 0 (0 turns the penalty off).  Call
+ * before dgm_bind.  Central flux and LSRK4 only, no PML, no mixed orders
+ * (DGM_EUNSUP).  Facets are numbered by (lower element, its local face),
+ * ascending; dgm_info gives their count and the facet buffer size.  The
+ * paired FP32 variants are then refused or skipped, like the adjoint and the
+ * batch.  No CUDA call. */
+int dgm_set_sip(dgm_plan* plan, double alpha);
+
+/* Caller-owned device buffers of the facet field (dgm_info.bytes_facets each;
+ * layout [3][NF][facet][column]: physical Cartesian components of h_s per
+ * face mode of the facet's face basis): hs0 holds the current facet state
+ * (zero for a start from rest) and alternates with hs1 like the field
+ * buffers; hs_res is the LSRK residual, and dgm_rhs writes dh_s/dt of the
+ * current facet state into it.  Call after dgm_bind.  dgm_energy does not
+ * include the facet energy. */
+int dgm_bind_sip(dgm_plan* plan, void* hs0, void* hs1, void* hs_res);
 
 /* Read and clear the device status word (synchronises).  Returns DGM_OK or
  * the latched device error. */

@@ -167,6 +167,13 @@ struct dgm_plan {
     size_t off_inc = 0, off_incv = 0;
     std::vector<double> inc_host;    // the FP64 table (layout at incident_eval)
     std::vector<int32_t> nbr_plain;  // neighbour table without incident codes
+    // interior penalty with a facet field (dgm_set_sip, dgm_bind_sip)
+    double sip_alpha = 0.0;          // 0: off
+    int64_t n_facets = 0;            // interior facets
+    size_t off_sfid = 0;             // [4][K] int32: (facet << 1) | owner, or -1
+    std::vector<int32_t> sfid_host;
+    void* hs[2] = {nullptr, nullptr};
+    void* hs_res = nullptr;
 };
 
 static thread_local std::string g_err;
@@ -397,6 +404,8 @@ static int plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt
         off = align256(off + size_t(kt->real_size) * 3 * P->NF * P->n_bfaces);
     }
     P->nbr_plain = P->mesh.nbr;
+    P->off_sfid = off;   // facet codes of the interior penalty
+    off = align256(off + sizeof(int32_t) * 4 * K);
     P->bytes_geom = off;
     P->k_active = K;
     P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
@@ -433,6 +442,8 @@ int dgm_plan_info(const dgm_plan* P, dgm_info* out) {
     out->bytes_geom = P->bytes_geom;
     out->n_quad = (P->pE + 3) * (P->pE + 3) * (P->pE + 3);
     out->N_H = P->NH;
+    out->n_facets = P->n_facets;
+    out->bytes_facets = size_t(P->n_facets) * P->opt.n_columns * 3 * P->NF * P->kt->real_size;
     return DGM_OK;
 }
 
@@ -539,6 +550,10 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
         (e = cudaMemcpyAsync(P->geom + P->off_inc, P->inc_host.data(), sizeof(double) * P->inc_host.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "upload incident table");
+    if (P->sip_alpha > 0.0 &&
+        (e = cudaMemcpyAsync(P->geom + P->off_sfid, P->sfid_host.data(), sizeof(int32_t) * 4 * K,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "upload facet codes");
     if (int rc = build_face_table(P)) return rc;
     // the host copies above are pageable: finish them before the host vectors can change
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
@@ -569,6 +584,21 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.K_active = P->k_active;
     prm.ops = P->bytes_ops ? static_cast<const void*>(P->geom + P->off_ops) : nullptr;
     prm.inc = P->n_inc > 0 ? static_cast<const void*>(P->geom + P->off_incv) : nullptr;
+    prm.sip_alpha = P->sip_alpha;
+    prm.n_facets = P->n_facets;
+    if (P->sip_alpha > 0.0 && P->hs[0] != nullptr) {
+        prm.sfid = reinterpret_cast<const int32_t*>(P->geom + P->off_sfid);
+        prm.hs = P->hs[P->cur];
+        prm.hs_out = P->hs[1 - P->cur];
+        prm.hs_res = P->hs_res;
+    }
+}
+
+// The facet buffers of one LSRK stage: input of the current state, output the other.
+static void sip_stage(const dgm_plan* P, StageParams& prm) {
+    if (prm.hs == nullptr) return;
+    prm.hs = P->hs[P->cur];
+    prm.hs_out = P->hs[1 - P->cur];
 }
 
 }  // extern "C"
@@ -584,6 +614,9 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
 //   s_m(t) = sum_q W[m][q] g(t - t0 - tau_q),  g(x) = cos(2 pi f0 x) exp(-x^2 / (2 s^2)),
 //   s = 1 / (2 pi bw): the face-mode traces of the E jump 2 E_inc (e+ = e- + 2 E_inc).
 // One warp per face: the lanes take the rule's points, then reduce per mode.
+// The delay x = t - t0 - tau_q is formed in FP64 (t may be large against the
+// pulse width); the pulse and the sums run in the plan's precision (an FP32
+// plan rounds the jump terms to FP32 anyway).
 template <typename R>
 __global__ void incident_eval(const double* __restrict__ tab, int NF, double t, R* __restrict__ out) {
     const int lane = threadIdx.x & 31;
@@ -591,31 +624,32 @@ __global__ void incident_eval(const double* __restrict__ tab, int NF, double t, 
     const int64_t nf = int64_t(tab[4]);
     if (i >= nf) return;
     const double twopi = 6.283185307179586476925286766559;
-    const double f0 = tab[0], sg = 1.0 / (twopi * tab[1]), t0 = tab[2];
+    const R f0 = R(tab[0]), sg = R(1.0 / (twopi * tab[1]));
+    const double t0 = tab[2];
     const int nq = int(tab[3]);
     const double* pts = tab + INC_HDR;
     const double* W = pts + 2 * nq;
     const double* fc = W + int64_t(NF) * nq + i * INC_FACE;
-    double g[INC_MAXQ / 32];
+    R g[INC_MAXQ / 32];
 #pragma unroll
     for (int k = 0; k < INC_MAXQ / 32; ++k) {
         const int q = lane + 32 * k;
-        g[k] = 0.0;
+        g[k] = R(0);
         if (q < nq) {
-            const double x = t - t0 - (fc[3] + pts[2 * q] * fc[4] + pts[2 * q + 1] * fc[5]);
-            g[k] = cos(twopi * f0 * x) * exp(-x * x / (2.0 * sg * sg));
+            const R x = R(t - t0 - (fc[3] + pts[2 * q] * fc[4] + pts[2 * q + 1] * fc[5]));
+            g[k] = cos(R(twopi) * f0 * x) * exp(-x * x / (R(2) * sg * sg));
         }
     }
     for (int m = 0; m < NF; ++m) {
-        double acc = 0.0;
+        R acc = R(0);
 #pragma unroll
         for (int k = 0; k < INC_MAXQ / 32; ++k) {
             const int q = lane + 32 * k;
-            if (q < nq) acc += W[int64_t(m) * nq + q] * g[k];
+            if (q < nq) acc += R(W[int64_t(m) * nq + q]) * g[k];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane < 3) out[(i * NF + m) * 3 + lane] = R(2.0 * fc[lane] * acc);
+        if (lane < 3) out[(i * NF + m) * 3 + lane] = R(2) * R(fc[lane]) * acc;
     }
 }
 
@@ -636,9 +670,16 @@ static int launch_stage(dgm_plan* P, StageParams& prm, int mode, cudaStream_t st
     return P->kt->launch_stage(prm, mode, st);
 }
 
-// The paired FP32 stage kernels (variants 3 and 4 up to p = 3) have no incident faces.
+// The paired FP32 stage kernels (variants 3 and 4 up to p = 3) have neither
+// incident faces nor the interior penalty.
 static bool variant_has_incident(const dgm_plan* P, int v) {
     return !(P->kt->real_size == 4 && P->opt.p <= 3 && (v == 3 || v == 4));
+}
+static bool needs_single_column_kernel(const dgm_plan* P) { return P->n_inc > 0 || P->sip_alpha > 0.0; }
+// The interior penalty is instantiated for the default tile shape only.
+static bool variant_ok(const dgm_plan* P, int v) {
+    if (P->sip_alpha > 0.0 && v != 0) return false;
+    return !needs_single_column_kernel(P) || variant_has_incident(P, v);
 }
 
 extern "C" {
@@ -769,6 +810,8 @@ int dgm_sample_receivers(dgm_plan* P, const void* fields, double* out_device) {
 
 int dgm_rhs(dgm_plan* P, const void* fields, const void* aux, void* dfields, void* daux, double t) {
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (P->sip_alpha > 0.0 && P->hs[0] == nullptr)
+        return fail(DGM_ESTATE, "facet buffers of the interior penalty not bound (dgm_bind_sip)");
     if (!fields || !dfields) return fail(DGM_EINVAL, "null field buffer");
     if (P->has_pml && P->mesh.npml > 0 && (!aux || !daux)) return fail(DGM_EINVAL, "PML plan needs aux/daux");
     StageParams prm;
@@ -778,6 +821,7 @@ int dgm_rhs(dgm_plan* P, const void* fields, const void* aux, void* dfields, voi
     prm.aux = aux;
     prm.aux_out = daux;
     prm.t = t;
+    if (prm.hs != nullptr) prm.hs_out = P->hs_res;   // dh_s/dt of the current facet field
     int rc = launch_stage(P, prm, MODE_RHS, P->stream);
     return rc ? fail(rc, "stage kernel launch failed") : DGM_OK;
 }
@@ -799,6 +843,8 @@ int dgm_leapfrog_start(dgm_plan* P, double t0) {
 
 int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (P->sip_alpha > 0.0 && P->hs[0] == nullptr)
+        return fail(DGM_ESTATE, "facet buffers of the interior penalty not bound (dgm_bind_sip)");
     if (n_steps < 0) return fail(DGM_EINVAL, "negative step count");
     StageParams prm;
     stage_params(P, prm);
@@ -816,6 +862,7 @@ int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
                 prm.t = t + LSRK_C[k] * dt;
                 prm.a = LSRK_A[k];
                 prm.b = LSRK_B[k];
+                sip_stage(P, prm);
                 int rc = launch_stage(P, prm, MODE_LSRK, P->stream);
                 if (rc) return fail(rc, "stage kernel launch failed");
                 P->cur = 1 - P->cur;
@@ -840,6 +887,8 @@ int dgm_current(const dgm_plan* P) { return P ? P->cur : -1; }
 
 int dgm_stage(dgm_plan* P, int32_t k, double t) {
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (P->sip_alpha > 0.0 && P->hs[0] == nullptr)
+        return fail(DGM_ESTATE, "facet buffers of the interior penalty not bound (dgm_bind_sip)");
     if (P->opt.integrator != DGM_LSRK4) return fail(DGM_ESTATE, "dgm_stage needs an LSRK4 plan");
     if (k < 0 || k > 4) return fail(DGM_EINVAL, "stage index must be 0..4");
     StageParams prm;
@@ -854,6 +903,7 @@ int dgm_stage(dgm_plan* P, int32_t k, double t) {
     prm.t = t + LSRK_C[k] * dt;
     prm.a = LSRK_A[k];
     prm.b = LSRK_B[k];
+    sip_stage(P, prm);
     int rc = launch_stage(P, prm, MODE_LSRK, P->stream);
     if (rc) return fail(rc, "stage kernel launch failed");
     P->cur = 1 - P->cur;
@@ -962,7 +1012,52 @@ int dgm_set_incident(dgm_plan* P, int64_t n, const int64_t* faces, const dgm_inc
 int dgm_set_active(dgm_plan* P, int64_t n) {
     if (!P) return fail(DGM_EINVAL, "null plan");
     if (n < 1 || n > P->mesh.K) return fail(DGM_EINVAL, "active element count must be in 1..K");
+    if (n < P->mesh.K && P->sip_alpha > 0.0)
+        return fail(DGM_EUNSUP, "the interior penalty needs every element active");
     P->k_active = n;
+    return DGM_OK;
+}
+
+int dgm_set_sip(dgm_plan* P, double alpha) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(DGM_EINVAL, "alpha must be finite and >= 0");
+    if (P->bound) return fail(DGM_ESTATE, "set the penalty before dgm_bind");
+    if (alpha > 0.0) {
+        if (P->opt.flux != DGM_CENTRAL) return fail(DGM_EUNSUP, "the interior penalty needs the central flux");
+        if (P->opt.integrator != DGM_LSRK4) return fail(DGM_EUNSUP, "the interior penalty needs LSRK4");
+        if (P->mixed) return fail(DGM_EUNSUP, "mixed-order plans have no interior penalty");
+        if (P->has_pml) return fail(DGM_EUNSUP, "the interior penalty is not built with a PML");
+        if (P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the interior penalty needs every element active");
+    }
+    const int64_t K = P->mesh.K;
+    P->sip_alpha = alpha;
+    P->n_facets = 0;
+    P->sfid_host.assign(size_t(4) * K, -1);
+    if (alpha == 0.0) return DGM_OK;
+    // facets numbered by (lower element, its local face), ascending; the lower
+    // element owns the facet (it advances h_s)
+    for (int64_t e = 0; e < K; ++e)
+        for (int f = 0; f < 4; ++f) {
+            const int32_t code = P->nbr_plain[size_t(f) * K + e];
+            if (code < 0 || int64_t(code >> 2) <= e) continue;
+            const int64_t e2 = code >> 2;
+            const int f2 = code & 3;
+            if (P->n_facets >= (int64_t(1) << 30)) return fail(DGM_EUNSUP, "too many facets");
+            P->sfid_host[size_t(f) * K + e] = int32_t((P->n_facets << 1) | 1);
+            P->sfid_host[size_t(f2) * K + e2] = int32_t(P->n_facets << 1);
+            ++P->n_facets;
+        }
+    P->variant = 0;
+    return DGM_OK;
+}
+
+int dgm_bind_sip(dgm_plan* P, void* hs0, void* hs1, void* hs_res) {
+    if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (!(P->sip_alpha > 0.0)) return fail(DGM_ESTATE, "no interior penalty on this plan");
+    if (!hs0 || !hs1 || !hs_res) return fail(DGM_EINVAL, "null facet buffer");
+    P->hs[0] = P->cur == 0 ? hs0 : hs1;   // hs0 holds the current state
+    P->hs[1] = P->cur == 0 ? hs1 : hs0;
+    P->hs_res = hs_res;
     return DGM_OK;
 }
 
@@ -1276,6 +1371,7 @@ extern "C" int dgm_batch_create(dgm_batch** out, dgm_plan* const* members, int32
             return fail(DGM_EINVAL, "batch members must have every element active (no halo)");
         if (members[i]->mixed) return fail(DGM_EUNSUP, "mixed-order plans are not batched");
         if (members[i]->n_inc > 0) return fail(DGM_EUNSUP, "plans with incident faces are not batched");
+        if (members[i]->sip_alpha > 0.0) return fail(DGM_EUNSUP, "plans with the interior penalty are not batched");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(DGM_EINVAL, "duplicate batch member");
     }
@@ -1492,6 +1588,7 @@ extern "C" int dgm_forward_record(dgm_plan* P, int64_t n_steps, double t0, doubl
     if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
     if (P && P->mixed) return fail(DGM_EUNSUP, "the adjoint is not built for mixed-order plans");
     if (P && P->n_inc > 0) return fail(DGM_EUNSUP, "the adjoint is not built for incident faces");
+    if (P && P->sip_alpha > 0.0) return fail(DGM_EUNSUP, "the adjoint is not built for the interior penalty");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (P->opt.integrator != DGM_LSRK4) return fail(DGM_EUNSUP, "the adjoint needs LSRK4");
     if (!records || !ws_ || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
@@ -1559,6 +1656,7 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
     if (P && P->k_active < P->mesh.K) return fail(DGM_EUNSUP, "the adjoint needs every element active");
     if (P && P->mixed) return fail(DGM_EUNSUP, "the adjoint is not built for mixed-order plans");
     if (P && P->n_inc > 0) return fail(DGM_EUNSUP, "the adjoint is not built for incident faces");
+    if (P && P->sip_alpha > 0.0) return fail(DGM_EUNSUP, "the adjoint is not built for the interior penalty");
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
     if (!drec || !ws_ || !deps || !dmu || n_steps < 1) return fail(DGM_EINVAL, "invalid arguments");
     if (reinterpret_cast<uintptr_t>(ws_) % 256) return fail(DGM_EINVAL, "workspace must be 256-byte aligned");
@@ -1659,6 +1757,8 @@ extern "C" int dgm_adjoint(dgm_plan* P, int64_t n_steps, double t0, const double
 // fastest for dgm_advance and dgm_batch_create.
 extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* ms_out) {
     if (!P || !P->bound) return fail(DGM_ESTATE, "plan not bound");
+    if (P->sip_alpha > 0.0 && P->hs[0] == nullptr)
+        return fail(DGM_ESTATE, "facet buffers of the interior penalty not bound (dgm_bind_sip)");
     if (!workspace) return fail(DGM_EINVAL, "null workspace");
     if (reps < 1) reps = 3;
     dgm_info info;
@@ -1721,7 +1821,7 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
     float best_ms = 1e30f;
     prm.tile_groups = 1;
     for (int v = 0; v < P->kt->n_variants && rc == DGM_OK; ++v) {
-        if (P->n_inc > 0 && !variant_has_incident(P, v)) {
+        if (!variant_ok(P, v)) {
             if (ms_out) ms_out[v] = 0.f;
             continue;
         }
@@ -1784,8 +1884,9 @@ extern "C" int dgm_autotune_info(const dgm_plan* P, int32_t* n_variants, int32_t
 extern "C" int dgm_set_variant(dgm_plan* P, int32_t v) {
     if (!P) return fail(DGM_EINVAL, "null plan");
     if (v < 0 || v >= P->kt->n_variants) return fail(DGM_EINVAL, "variant out of range");
-    if (P->n_inc > 0 && !variant_has_incident(P, v))
-        return fail(DGM_EUNSUP, "the paired stage variants have no incident faces");
+    if (!variant_ok(P, v))
+        return fail(DGM_EUNSUP, "this stage variant has neither incident faces nor the penalty "
+                                "(the penalty runs in the default shape)");
     P->variant = v;
     return DGM_OK;
 }

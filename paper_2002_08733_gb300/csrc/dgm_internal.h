@@ -111,6 +111,16 @@ struct StageParams {
     const void* ops;      // mixed-order plans: dense reference operators S, R of degree p + 1
     const void* inc;      // incident faces: [i][NF][3] reference-frame jump terms
                           // 2 A^T E_inc traced on face mode m at the stage time (R), or null
+    // interior penalty with a facet field (null when off): per (face, element)
+    // (facet << 1) | owner, or -1 ([4][K]); facet field h_s [3][NF][facet][S]
+    // (physical components per face mode, R): stage input, output (LSRK; the
+    // time derivative for MODE_RHS) and LSRK residual; the penalty alpha; facets
+    const int32_t* sfid;
+    const void* hs;
+    void* hs_out;
+    void* hs_res;
+    double sip_alpha;
+    int64_t n_facets;
 };
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms

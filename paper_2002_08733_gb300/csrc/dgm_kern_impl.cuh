@@ -114,11 +114,18 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
                                                : launch_pair_ix<int64_t>(q, grid, st);
 }
 #else
-template <typename IX>
+// the interior penalty's kernels: LSRK and right-hand-side modes, default tile shape
+#if !defined(DGM_TE) && !defined(DGM_TC)
+constexpr bool kSIP = (DGM_MODE == MODE_LSRK || DGM_MODE == MODE_RHS);
+#else
+constexpr bool kSIP = false;
+#endif
+
+template <typename IX, bool SIP>
 int launch_ix(const StageParams& q, unsigned grid, cudaStream_t st) {
-    constexpr size_t smem = stage_smem_bytes<kP, Real, kTE, kTC>();
+    constexpr size_t smem = stage_smem_bytes<kP, Real, kTE, kTC, SIP>();
     static bool configured = false;
-    auto k = stage_kernel<kP, Real, kTE, kNT, DGM_MODE, IX, kTC>;
+    auto k = stage_kernel<kP, Real, kTE, kNT, DGM_MODE, IX, kTC, SIP>;
     if (kTC && q.tc_b == nullptr) return DGM_EUNSUP;   // no operator image for this plan
     if (!configured) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
@@ -149,8 +156,15 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     q.dt_f = float(prm.dt);
     q.a_f = float(prm.a);
     q.b_f = float(prm.b);
-    return (!q.force_index64 && fits_32bit(q)) ? launch_ix<uint32_t>(q, grid, st)
-                                               : launch_ix<int64_t>(q, grid, st);
+    const bool i32 = !q.force_index64 && fits_32bit(q);
+    if (q.hs != nullptr) {   // interior penalty
+        if constexpr (kSIP) {
+            return i32 ? launch_ix<uint32_t, true>(q, grid, st) : launch_ix<int64_t, true>(q, grid, st);
+        } else {
+            return DGM_EUNSUP;
+        }
+    }
+    return i32 ? launch_ix<uint32_t, false>(q, grid, st) : launch_ix<int64_t, false>(q, grid, st);
 }
 #endif
 

@@ -75,11 +75,12 @@ enum FaceConst {
     FC_BND = 17   // 1 on a PEC face
 };
 constexpr int EG = 16;   // element constants per column (same slots as G_*)
-constexpr int NBS = 4;   // neighbour codes per column staged in shared memory
+constexpr int NBS = 4;   // neighbour codes per column staged in shared memory (+4 facet
+                         // codes with the interior penalty)
 
 // Face constants of the stage kernel, whose flux works in the element's
 // reference frame (see face_constants_ref), per (face, column).
-constexpr int FGR = 15;
+constexpr int FGR = 15;   // (16 with the interior penalty: FR_KS)
 enum FaceConstRef {
     FR_Q = 0,     // Q = A^T A_n^-T (9, row major): neighbour reference components -> own
     FR_NAE = 9,   // -alpha_E: -1 on an interior face, -2 on a PEC face (e+ = -e-)
@@ -88,15 +89,20 @@ enum FaceConstRef {
     FR_CE = 11,   // s_T c_E
     FR_BE = 12,   // b_E / (|det A| |A^-T m_f|)
     FR_CH = 13,   // s_T c_H
-    FR_BH = 14    // b_H / (|det A| |A^-T m_f|)
+    FR_BH = 14,   // b_H / (|det A| |A^-T m_f|)
+    FR_KS = 15    // interior penalty, on the facet's owner side: (alpha / mu_F) / (det A |A^-T m_f|)
 };
 constexpr int GM = 6;    // metric A^T A per column: entries 00, 01, 02, 11, 12, 22
+constexpr int GA = 9;    // A^T per column, row major (interior penalty only)
+template <bool SIP> __host__ __device__ constexpr int fgr() { return SIP ? FGR + 1 : FGR; }
+template <bool SIP> __host__ __device__ constexpr int nbs_rows() { return SIP ? 2 * NBS : NBS; }
 
-template <int P, typename R, int TE, bool TC = false>
+template <int P, typename R, int TE, bool TC = false, bool SIP = false>
 __host__ __device__ constexpr size_t stage_smem_bytes() {
     // tensor-core variant: + an mbarrier and the tensor-memory base (the operator
     // image lives in the neighbour-trace array, dead after phase 3)
-    return sizeof(R) * size_t(TE) * (6 * nmodes(P) + 48 * nfmodes(P) + 4 * FGR + EG + GM + NBS) +
+    return sizeof(R) * size_t(TE) *
+               (6 * nmodes(P) + 48 * nfmodes(P) + 4 * fgr<SIP>() + EG + GM + (SIP ? GA : 0) + nbs_rows<SIP>()) +
            (TC ? size_t(32) : size_t(0));
 }
 
@@ -191,10 +197,13 @@ __device__ __forceinline__ void face_constants_tab(int f, const R (&ait)[9], R d
 // is not needed.
 // incident: a boundary face through which an incident field enters (ghost state
 // e+ = e- + 2 E_inc, h+ = -h-, Z+ = Z-; the E_inc part is added by flux_face).
-template <typename R, int TE>
+// ks_num: alpha / mu_F on the owner side of a penalised interior face, else 0.
+// ga (with gm, face 0 only): the element's A^T, row major, for the penalty.
+template <typename R, int TE, bool SIP>
 __device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R det, R epsm, R mum,
                                                    bool has_nbr, const R (&aitn)[9], R zn,
-                                                   int upwind, R* fc, R* gm, bool incident = false) {
+                                                   int upwind, R* fc, R* gm, bool incident,
+                                                   R ks_num, R* ga) {
     // A^T = det A adj(A^-T), row major
     R at[9];
     at[0] = ait[4] * ait[8] - ait[5] * ait[7];
@@ -239,7 +248,12 @@ __device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R d
     fc[FR_BE * TE] = kb * be;
     fc[FR_CH * TE] = st * ch;
     fc[FR_BH * TE] = kb * bh;
+    if constexpr (SIP) fc[FR_KS * TE] = ks_num * st * kb;
     if (gm != nullptr) {
+        if constexpr (SIP) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) ga[k * TE] = at[k];
+        }
         gm[0 * TE] = at[0] * at[0] + at[1] * at[1] + at[2] * at[2];
         gm[1 * TE] = at[0] * at[3] + at[1] * at[4] + at[2] * at[5];
         gm[2 * TE] = at[0] * at[6] + at[1] * at[7] + at[2] * at[8];
@@ -254,16 +268,98 @@ __host__ __device__ constexpr int sym3(int i, int j) {
     return i > j ? sym3(j, i) : (i == 0 ? j : (i == 1 ? 2 + j : 5));
 }
 
+// Interior penalty (phase 3 of the kernels instantiated with the penalty).
+// Owner side of face F, before its own traces become fluxes:
+// dh_s/dt = -(alpha / mu_F) A (m_f x de) / (det A |A^-T m_f|) per mode, with the
+// interior reference jump de = Q e+ - e-, and the facet field's stage update.
+template <int F, int NF, typename R, int TE, int MODE>
+__device__ __forceinline__ void sip_owner(int m0, int m1, int c, const R* trO, const R* trN, const R* d,
+                                       const R* hsv, R* hso, R* hsr, int64_t fs, const R* gac, R ca,
+                                       R cb, R dtc) {
+    constexpr int A = F == 0 ? -1 : F - 1;
+    constexpr int B = F % 3, CC = (F + 1) % 3;
+    R q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) q[k] = k / 3 != A ? d[(FR_Q + k) * TE] : R(0);
+    R at[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) at[k] = gac[k * TE];
+    const R ks = d[FR_KS * TE];
+#pragma unroll 1
+    for (int m = m0; m < m1; ++m) {
+        const R* own = trO + (F * 6 * NF + m) * TE + c;
+        const R* nbt = trN + (F * 6 * NF + m) * TE + c;
+        R de[3] = {0, 0, 0};
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            if (r != A)
+                de[r] = q[3 * r] * nbt[0] + q[3 * r + 1] * nbt[NF * TE] + q[3 * r + 2] * nbt[2 * NF * TE] -
+                        own[r * NF * TE];
+        R v[3];
+        if (F == 0) {
+            v[0] = de[2] - de[1];
+            v[1] = de[0] - de[2];
+            v[2] = de[1] - de[0];
+        } else {
+            v[A] = R(0);
+            v[B] = de[CC];
+            v[CC] = -de[B];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const R r = -ks * (at[k] * v[0] + at[3 + k] * v[1] + at[6 + k] * v[2]);
+            const int64_t j = int64_t(k * NF + m) * fs;
+            if (MODE == MODE_RHS) {
+                hso[j] = r;
+            } else {
+                const R rr = ca * hsr[j] + dtc * r;
+                hsr[j] = rr;
+                hso[j] = hsv[j] + cb * rr;
+            }
+        }
+    }
+}
+
+// Both sides of face F, after the fluxes: the pulled-back E flux gains
+// s_T m_f x (A^T h_s) (central flux, c_E = 1/2, so s_T = 2 cE).
+template <int F, int NF, typename R, int TE>
+__device__ __forceinline__ void sip_eflux(int m0, int m1, int c, R* trO, const R* hsv, int64_t fs,
+                                       const R* gac, R cE) {
+    constexpr int B = F % 3, CC = (F + 1) % 3;
+    R at[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) at[k] = gac[k * TE];
+    const R sT = R(2) * cE;
+#pragma unroll 1
+    for (int m = m0; m < m1; ++m) {
+        R* own = trO + (F * 6 * NF + m) * TE + c;
+        R y[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            y[j] = at[3 * j] * hsv[m * fs] + at[3 * j + 1] * hsv[(NF + m) * fs] +
+                   at[3 * j + 2] * hsv[(2 * NF + m) * fs];
+        if (F == 0) {
+            own[0 * NF * TE] += sT * (y[2] - y[1]);
+            own[1 * NF * TE] += sT * (y[0] - y[2]);
+            own[2 * NF * TE] += sT * (y[1] - y[0]);
+        } else {
+            own[B * NF * TE] += sT * y[CC];
+            own[CC * NF * TE] -= sT * y[B];
+        }
+    }
+}
+
 // Numerical flux of modes [m0, m1) of face F (compile time) in the reference
 // frame (face_constants_ref): reads both sides' reference traces, overwrites
 // the own traces with the pulled-back fluxes g.  On an axis face only the two
 // non-zero components of g are written.  FULL: the own trace has all three
 // components and the physical jumps M dx are stored for the adjoint.
-template <int F, int NF, typename R, int TE, int MODE, typename IX>
+template <int F, int NF, typename R, int TE, int MODE, typename IX, bool SIP>
 __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R* trN,
                                           const R* fg, const R* gm, const R* eg, R* jumps,
-                                          IX C, IX col, bool active, int32_t code = -1,
-                                          const void* incp = nullptr) {
+                                          IX C, IX col, bool active, int32_t code,
+                                          const void* incp, const R* hsv, R* hso, R* hsr,
+                                          int64_t fs, const R* gac, R ca, R cb, R dtc) {
     constexpr bool DO_E = (MODE != MODE_LF_H);   // E fluxes needed
     constexpr bool DO_H = (MODE != MODE_LF_E);   // H fluxes needed
     constexpr bool HAS_E = (MODE != MODE_LF_E);  // E jump used (H flux, upwind E flux)
@@ -271,7 +367,7 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
     constexpr bool FULL = (MODE == MODE_RAW);
     constexpr int A = F == 0 ? -1 : F - 1;       // axis of m_f = -e_A
     constexpr int B = F % 3, CC = (F + 1) % 3;   // the other two axes, (A, B, CC) cyclic
-    const R* d = fg + F * FGR * TE + c;
+    const R* d = fg + F * fgr<SIP>() * TE + c;
     R q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) q[k] = (FULL || k / 3 != A) ? d[(FR_Q + k) * TE] : R(0);
@@ -293,6 +389,9 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
     const R gcb = gsym(CC, B), gcc = gsym(CC, CC), gbb = gsym(B, B);
     const R kEcb = bE * gcb, kEcc = bE * gcc, kEbb = bE * gbb;
     const R kHcb = bH * gcb, kHcc = bH * gcc, kHbb = bH * gbb;
+    if constexpr (SIP) {
+        if (hso != nullptr) sip_owner<F, NF, R, TE, MODE>(m0, m1, c, trO, trN, d, hsv, hso, hsr, fs, gac, ca, cb, dtc);
+    }
     // incident face (e+ = e- + 2 E_inc): the E jump is the incident term alone
     const R* inc = (HAS_E && code <= -2 && incp != nullptr && active)
                        ? static_cast<const R*>(incp) + IX(-code - 2) * NF * 3
@@ -370,6 +469,9 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
             }
         }
     }
+    if constexpr (SIP) {
+        if (hsv != nullptr) sip_eflux<F, NF, R, TE>(m0, m1, c, trO, hsv, fs, gac, cE);
+    }
 }
 
 // Right-hand side rows [LO, HI) of component `comp` (before the mass inverse):
@@ -439,9 +541,15 @@ __device__ __forceinline__ void rhs_part(int part, int comp, int c, const R* us,
 // tensor cores (dgm_tc.cuh, TcShape), with tensor-memory row (field, column);
 // phase 5 reads the pre-mass right-hand side from tensor memory.  The other
 // phases are shared with the SIMT kernel.
-template <int P, typename R, int TE, int NT, int MODE, typename IX = int64_t, bool TC = false>
+// SIP: interior penalty with a facet field (LSRK and right-hand-side modes of
+// the SIMT kernel): facet codes staged in phase 1, A^T and one more face
+// constant, the facet terms in phase 3 (sip_owner, sip_eflux).
+template <int P, typename R, int TE, int NT, int MODE, typename IX = int64_t, bool TC = false,
+          bool SIP = false>
 __global__ void __launch_bounds__(NT, TC ? 1 : ((sizeof(R) == 8 || P <= 3) ? 2 : 1))
 stage_kernel(const StageParams prm) {
+    static_assert(!SIP || (!TC && (MODE == MODE_LSRK || MODE == MODE_RHS)), "interior penalty modes");
+    constexpr int FGRT = fgr<SIP>();
     constexpr int N = nmodes(P);
     constexpr int NF = nfmodes(P);
     constexpr int NG = NT / TE;                         // column groups working side by side
@@ -452,17 +560,18 @@ stage_kernel(const StageParams prm) {
     R* us = reinterpret_cast<R*>(smem_raw);      // [6N][TE]
     R* trO = us + 6 * N * TE;                    // [4][6][NF][TE]  own traces -> g
     R* trN = trO + 24 * NF * TE;                 // [4][6][NF][TE]  nbr traces -> rhs [6][N][TE]
-    R* fg = trN + 24 * NF * TE;                  // [4][FGR][TE]
-    R* eg = fg + 4 * FGR * TE;                   // [EG][TE]
+    R* fg = trN + 24 * NF * TE;                  // [4][FGRT][TE]
+    R* eg = fg + 4 * FGRT * TE;                  // [EG][TE]
     R* gm = eg + EG * TE;                        // [GM][TE] metric A^T A
-    int32_t* nbs = reinterpret_cast<int32_t*>(gm + GM * TE);   // [4][TE] neighbour codes
+    R* ga = gm + GM * TE;                        // [GA][TE] A^T (interior penalty only)
+    int32_t* nbs = reinterpret_cast<int32_t*>(ga + (SIP ? GA : 0) * TE);   // neighbour (+ facet) codes
     static_assert(!TC || (sizeof(R) == 4 && TE == 64 && (MODE == MODE_LSRK || MODE == MODE_RHS) &&
                           (NT / TE) % 2 == 0 && TcShape<P>::FITS),
                   "tensor-core variant: FP32, 64 columns, LSRK or right-hand side, even groups");
     // tensor-core variant: mbarrier and tensor-memory base address after the
     // tables; the operator image goes into the neighbour-trace array in phase 4
     uint64_t* tc_bar = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(nbs + NBS * TE) + 7) & ~uintptr_t(7));
+        (reinterpret_cast<uintptr_t>(nbs + nbs_rows<SIP>() * TE) + 7) & ~uintptr_t(7));
     uint32_t* tc_base = reinterpret_cast<uint32_t*>(tc_bar + 1);
     if constexpr (TC) {
         static_assert(TcShape<P>::B_BYTES <= int(sizeof(R)) * 24 * nfmodes(P) * TE,
@@ -487,7 +596,11 @@ stage_kernel(const StageParams prm) {
     const int s = active ? int(col - e * S) : 0;
     const R* u = static_cast<const R*>(prm.u);   // may alias u_out (leapfrog)
     const R* gr = static_cast<const R*>(prm.geo_r);
-    if (grp < 4) nbs[grp * TE + c] = active ? prm.nbr[IX(grp) * K + e] : -1;
+    // stage coefficients in the kernel's precision: FP32 kernels read the FP32
+    // copies, so that no conversion runs on the FP64 pipe
+    auto coef = [&](double d, float f) { return sizeof(R) == 4 ? R(f) : R(d); };
+    for (int r = grp; r < nbs_rows<SIP>(); r += NG)   // neighbour codes, then facet codes (-1: none)
+        nbs[r * TE + c] = !active ? -1 : r < 4 ? prm.nbr[IX(r) * K + e] : prm.sfid[IX(r - 4) * K + e];
 
     // ---- phase 1: tile coefficients, element and face constants --------------
     // Groups 0..3 compute the face constants of face f = group from the
@@ -524,9 +637,18 @@ stage_kernel(const StageParams prm) {
         const R epsm = active ? gr[IX(G_EPS) * K + e] : R(1);
         const R mum = active ? gr[IX(G_MU) * K + e] : R(1);
         const R zn = active ? fn[IX(FNB_Z) * K] : R(1);
-        face_constants_ref<R, TE>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
-                                  prm.upwind, fg + f * FGR * TE + c, f == 0 ? gm + c : nullptr,
-                                  code <= -2 && prm.inc != nullptr);
+        // interior penalty on the facet's owner side: alpha / mu_F, mu_F the mean of both sides
+        R ksn = R(0);
+        if constexpr (SIP) {
+            if (active) {
+                const int32_t sf = prm.sfid[IX(f) * K + e];
+                if (sf >= 0 && (sf & 1))
+                    ksn = R(prm.sip_alpha) / (R(0.5) * (mum + fn[IX(FNB_MU) * K]));
+            }
+        }
+        face_constants_ref<R, TE, SIP>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
+                                       prm.upwind, fg + f * FGRT * TE + c, f == 0 ? gm + c : nullptr,
+                                  code <= -2 && prm.inc != nullptr, ksn, ga + c);
     };
     // neighbour code of this group's round-0 item, loaded with the other
     // independent loads so that the dependent gather starts one round trip in
@@ -652,11 +774,29 @@ stage_kernel(const StageParams prm) {
             const int ch = it % CHUNKS;
             const int m0 = ch * NF / CHUNKS, m1 = (ch + 1) * NF / CHUNKS;
             const int32_t fcode = nbs[f * TE + c];
+            // interior penalty: this column's facet field on face f (and, on the
+            // owner side, its output and residual), [3][NF][facet][S]: mode-major,
+            // so that the facets of neighbouring columns sit side by side
+            const R* hsv = nullptr;
+            R *hso = nullptr, *hsr = nullptr;
+            const int64_t fs = int64_t(prm.n_facets) * S;
+            if (SIP && active) {
+                const int32_t sf = nbs[(4 + f) * TE + c];
+                if (sf >= 0) {
+                    const IX off = IX(sf >> 1) * S + s;
+                    hsv = static_cast<const R*>(prm.hs) + off;
+                    if (sf & 1) {
+                        hso = static_cast<R*>(prm.hs_out) + off;
+                        hsr = MODE == MODE_LSRK ? static_cast<R*>(prm.hs_res) + off : nullptr;
+                    }
+                }
+            }
+            const R ca = coef(prm.a, prm.a_f), cb = coef(prm.b, prm.b_f), dtc = coef(prm.dt, prm.dt_f);
             switch (f) {
-                case 0: flux_face<0, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
-                case 1: flux_face<1, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
-                case 2: flux_face<2, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
-                default: flux_face<3, NF, R, TE, MODE, IX>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc); break;
+                case 0: flux_face<0, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
+                case 1: flux_face<1, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
+                case 2: flux_face<2, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
+                default: flux_face<3, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
             }
         }
     }
@@ -674,9 +814,6 @@ stage_kernel(const StageParams prm) {
     constexpr bool P5_EVEN = (N % NP5) == 0;          // every part has exactly RP5 rows
     constexpr bool PREFETCH_RES = (MODE == MODE_LSRK);
     R resv[PREFETCH_RES ? 3 : 1][PREFETCH_RES ? RP5 : 1];
-    // stage coefficients in the kernel's precision: FP32 kernels read the FP32
-    // copies, so that no conversion runs on the FP64 pipe
-    auto coef = [&](double d, float f) { return sizeof(R) == 4 ? R(f) : R(d); };
     if (PREFETCH_RES && grp < 2 * NP5) {
         const int fb = (grp / NP5) * 3, part = grp % NP5;
         const int lo = part * N / NP5, hi = (part + 1) * N / NP5;

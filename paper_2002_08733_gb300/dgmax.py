@@ -58,7 +58,8 @@ class Info(ctypes.Structure):
                 ("NF", ctypes.c_int32), ("S", ctypes.c_int32), ("real_size", ctypes.c_int32),
                 ("bytes_fields", ctypes.c_size_t), ("bytes_aux", ctypes.c_size_t),
                 ("bytes_geom", ctypes.c_size_t), ("n_quad", ctypes.c_int32),
-                ("N_H", ctypes.c_int32)]
+                ("N_H", ctypes.c_int32), ("n_facets", ctypes.c_int64),
+                ("bytes_facets", ctypes.c_size_t)]
 
 
 _lib = None
@@ -107,6 +108,8 @@ _SIGS = {
     "dgm_halo_unpack": [_P, _P, _P, ctypes.c_int64, _P],
     "dgm_stage": [_P, ctypes.c_int32, ctypes.c_double],
     "dgm_set_incident": [_P, ctypes.c_int64, _P, ctypes.POINTER(Incident)],
+    "dgm_set_sip": [_P, ctypes.c_double],
+    "dgm_bind_sip": [_P, _P, _P, _P],
     "dgm_last_error": [],
     "dgm_plan_destroy": [_P],
 }
@@ -148,8 +151,10 @@ class Plan:
     """Host-side plan (mesh setup, reference matrices); no GPU needed."""
 
     def __init__(self, xyz, tets, eps, mu, p, precision="fp64", flux="upwind",
-                 integrator="lsrk4", dt=1e-3, S=1, pml=None, max_receivers=0, mixed=False):
-        """mixed=True: E of degree p + 1, H of degree p (dgm_plan_create_mixed)."""
+                 integrator="lsrk4", dt=1e-3, S=1, pml=None, max_receivers=0, mixed=False,
+                 sip=None):
+        """mixed=True: E of degree p + 1, H of degree p (dgm_plan_create_mixed);
+        sip=alpha: interior penalty with a facet field (dgm_set_sip)."""
         lib = load_library()
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         tets = np.ascontiguousarray(tets, dtype=np.int64)
@@ -177,6 +182,9 @@ class Plan:
         self.handle = h
         self.opt = opt
         self.precision = precision
+        if sip:
+            _check(lib.dgm_set_sip(h, float(sip)))
+        self.sip = float(sip or 0.0)
         info = Info()
         _check(lib.dgm_plan_info(h, ctypes.byref(info)))
         self.info = info
@@ -249,6 +257,15 @@ class Solver(Plan):
         _check(_lib.dgm_bind(self.handle, self.geom_view.data_ptr(), _ptr(self.fields[0]),
                              _ptr(self.fields[1]), _ptr(self.res), _ptr(self.aux[0]),
                              _ptr(self.aux[1]), _ptr(self.aux_res), self.stream.cuda_stream))
+        self.hs = [None, None]
+        self.hs_res = None
+        if self.sip:   # facet field of the interior penalty: [3][NF][facet][column], from rest
+            fshape = (3, i.NF, i.n_facets, self.S)
+            self.hs = [torch.zeros(fshape, dtype=dt, device=self.device) for _ in range(2)]
+            self.hs_res = torch.zeros(fshape, dtype=dt, device=self.device)
+            torch.cuda.synchronize(self.device)
+            _check(_lib.dgm_bind_sip(self.handle, _ptr(self.hs[self.current()]),
+                                     _ptr(self.hs[1 - self.current()]), _ptr(self.hs_res)))
 
     # -- layout conversion between (K, S, 6, N) and the device layout [6][N][K][S]
     #    (mixed-order plans: H modes l >= N_H of the (K, S, 6, N) array are zero)
@@ -294,6 +311,23 @@ class Solver(Plan):
     def state(self):
         self.torch.cuda.synchronize(self.device)
         return self.from_device(self.fields[self.current()])
+
+    def facet_state(self):
+        """Facet field of the interior penalty -> (n_facets, S, 3, NF) float64."""
+        self.torch.cuda.synchronize(self.device)
+        return np.transpose(self.hs[self.current()].double().cpu().numpy(), (2, 3, 0, 1)).copy()
+
+    def facet_rhs(self):
+        """dh_s/dt written by the last rhs() call -> (n_facets, S, 3, NF)."""
+        self.torch.cuda.synchronize(self.device)
+        return np.transpose(self.hs_res.double().cpu().numpy(), (2, 3, 0, 1)).copy()
+
+    def set_facet_state(self, hs):
+        """hs: (n_facets, S, 3, NF)."""
+        self.torch.cuda.synchronize(self.device)
+        t = self.torch.as_tensor(np.ascontiguousarray(np.transpose(np.asarray(hs), (2, 3, 0, 1))))
+        self.hs[self.current()].copy_(t.to(self.hs[0]))
+        self.torch.cuda.synchronize(self.device)
 
     def rhs(self, u, aux=None, t=0.0):
         """One right-hand-side evaluation; u: (K, S, 6, N) array -> du (same shape)."""

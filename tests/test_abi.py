@@ -217,3 +217,27 @@ def test_incident_faces_are_validated_on_the_host(lib):
                  D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", "central", "leapfrog", 1e-3)):
         with pytest.raises(D.DgmError):
             plan.set_incident(z0, **wave)
+
+
+def test_interior_penalty_plan_sizes_and_limits(lib):
+    """dgm_set_sip: interior facets of a Kuhn grid, (4K - 12 n^2) / 2 of them;
+    central flux and LSRK4 only, no PML, no mixed orders, alpha >= 0."""
+    from paper_2002_08733_gb300 import dgmax as D
+    n = 3
+    xyz, tets = W.kuhn_mesh(n)
+    K = len(tets)
+    for p, prec, rs in ((1, "fp64", 8), (3, "fp32", 4)):
+        pl = D.Plan(xyz, tets, 1.0, 1.0, p, prec, "central", "lsrk4", 1e-3, S=2, sip=5.0)
+        nF = (4 * K - 12 * n * n) // 2
+        assert pl.info.n_facets == nF
+        assert pl.info.bytes_facets == nF * 2 * 3 * W.n_face_modes(p) * rs
+        assert lib.dgm_set_variant(pl.handle, 3 if prec == "fp32" else 0) == (3 if prec == "fp32" else 0)
+    assert D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", "central", "lsrk4", 1e-3).info.n_facets == 0
+    pml = dict(lo=(0.25,) * 3, hi=(0.75,) * 3, thickness=0.25, sigma_max=10.0)
+    for kw in (dict(flux="upwind"), dict(integrator="leapfrog"), dict(mixed=True), dict(pml=pml),
+               dict(sip=-1.0)):
+        args = dict(flux="central", integrator="lsrk4", sip=5.0)
+        args.update(kw)
+        with pytest.raises(D.DgmError):
+            D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", args.pop("flux"), args.pop("integrator"), 1e-3,
+                   **args)
