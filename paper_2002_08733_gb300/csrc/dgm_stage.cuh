@@ -272,12 +272,24 @@ __host__ __device__ constexpr int sym3(int i, int j) {
 // Owner side of face F, before its own traces become fluxes:
 // dh_s/dt = -(alpha / mu_F) A (m_f x de) / (det A |A^-T m_f|) per mode, with the
 // interior reference jump de = Q e+ - e-, and the facet field's stage update.
-template <int F, int NF, typename R, int TE, int MODE>
+template <int F, int NF, typename R, int TE, int MODE, int MC>
 __device__ __forceinline__ void sip_owner(int m0, int m1, int c, const R* trO, const R* trN, const R* d,
-                                       const R* hsv, R* hso, R* hsr, int64_t fs, const R* gac, R ca,
-                                       R cb, R dtc) {
+                                          const R* hsv, R* hso, R* hsr, int64_t fs, const R* gac, R ca,
+                                          R cb, R dtc) {
     constexpr int A = F == 0 ? -1 : F - 1;
     constexpr int B = F % 3, CC = (F + 1) % 3;
+    // the item's facet values first (at most MC modes), so that their round
+    // trips overlap instead of following one another mode by mode
+    R hv[MC][3], rv[MC][3];
+#pragma unroll
+    for (int i = 0; i < MC; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int64_t j = int64_t(k * NF + m0 + i) * fs;
+            const bool ok = MODE == MODE_LSRK && m0 + i < m1;
+            hv[i][k] = ok ? hsv[j] : R(0);
+            rv[i][k] = ok ? hsr[j] : R(0);
+        }
     R q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) q[k] = k / 3 != A ? d[(FR_Q + k) * TE] : R(0);
@@ -285,8 +297,10 @@ __device__ __forceinline__ void sip_owner(int m0, int m1, int c, const R* trO, c
 #pragma unroll
     for (int k = 0; k < 9; ++k) at[k] = gac[k * TE];
     const R ks = d[FR_KS * TE];
-#pragma unroll 1
-    for (int m = m0; m < m1; ++m) {
+#pragma unroll
+    for (int i = 0; i < MC; ++i) {
+        const int m = m0 + i;
+        if (m >= m1) break;
         const R* own = trO + (F * 6 * NF + m) * TE + c;
         const R* nbt = trN + (F * 6 * NF + m) * TE + c;
         R de[3] = {0, 0, 0};
@@ -312,32 +326,38 @@ __device__ __forceinline__ void sip_owner(int m0, int m1, int c, const R* trO, c
             if (MODE == MODE_RHS) {
                 hso[j] = r;
             } else {
-                const R rr = ca * hsr[j] + dtc * r;
+                const R rr = ca * rv[i][k] + dtc * r;
                 hsr[j] = rr;
-                hso[j] = hsv[j] + cb * rr;
+                hso[j] = hv[i][k] + cb * rr;
             }
         }
     }
 }
 
 // Both sides of face F, after the fluxes: the pulled-back E flux gains
-// s_T m_f x (A^T h_s) (central flux, c_E = 1/2, so s_T = 2 cE).
-template <int F, int NF, typename R, int TE>
+// s_T m_f x (A^T h_s) (central flux, c_E = 1/2, so s_T = 2 cE); the item's
+// facet values (at most MC modes) are loaded first.
+template <int F, int NF, typename R, int TE, int MC>
 __device__ __forceinline__ void sip_eflux(int m0, int m1, int c, R* trO, const R* hsv, int64_t fs,
-                                       const R* gac, R cE) {
+                                          const R* gac, R cE) {
     constexpr int B = F % 3, CC = (F + 1) % 3;
+    R hv[MC][3];
+#pragma unroll
+    for (int i = 0; i < MC; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) hv[i][k] = m0 + i < m1 ? hsv[int64_t(k * NF + m0 + i) * fs] : R(0);
     R at[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) at[k] = gac[k * TE];
     const R sT = R(2) * cE;
-#pragma unroll 1
-    for (int m = m0; m < m1; ++m) {
+#pragma unroll
+    for (int i = 0; i < MC; ++i) {
+        const int m = m0 + i;
+        if (m >= m1) break;
         R* own = trO + (F * 6 * NF + m) * TE + c;
         R y[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            y[j] = at[3 * j] * hsv[m * fs] + at[3 * j + 1] * hsv[(NF + m) * fs] +
-                   at[3 * j + 2] * hsv[(2 * NF + m) * fs];
+        for (int j = 0; j < 3; ++j) y[j] = at[3 * j] * hv[i][0] + at[3 * j + 1] * hv[i][1] + at[3 * j + 2] * hv[i][2];
         if (F == 0) {
             own[0 * NF * TE] += sT * (y[2] - y[1]);
             own[1 * NF * TE] += sT * (y[0] - y[2]);
@@ -354,7 +374,7 @@ __device__ __forceinline__ void sip_eflux(int m0, int m1, int c, R* trO, const R
 // the own traces with the pulled-back fluxes g.  On an axis face only the two
 // non-zero components of g are written.  FULL: the own trace has all three
 // components and the physical jumps M dx are stored for the adjoint.
-template <int F, int NF, typename R, int TE, int MODE, typename IX, bool SIP>
+template <int F, int NF, typename R, int TE, int MODE, typename IX, bool SIP, int MC = 1>
 __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R* trN,
                                           const R* fg, const R* gm, const R* eg, R* jumps,
                                           IX C, IX col, bool active, int32_t code,
@@ -368,6 +388,12 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
     constexpr int A = F == 0 ? -1 : F - 1;       // axis of m_f = -e_A
     constexpr int B = F % 3, CC = (F + 1) % 3;   // the other two axes, (A, B, CC) cyclic
     const R* d = fg + F * fgr<SIP>() * TE + c;
+    // interior penalty, owner side, first: it reads the traces before they
+    // become fluxes, and nothing of the flux is live yet
+    if constexpr (SIP) {
+        if (hso != nullptr)
+            sip_owner<F, NF, R, TE, MODE, MC>(m0, m1, c, trO, trN, d, hsv, hso, hsr, fs, gac, ca, cb, dtc);
+    }
     R q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) q[k] = (FULL || k / 3 != A) ? d[(FR_Q + k) * TE] : R(0);
@@ -389,9 +415,6 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
     const R gcb = gsym(CC, B), gcc = gsym(CC, CC), gbb = gsym(B, B);
     const R kEcb = bE * gcb, kEcc = bE * gcc, kEbb = bE * gbb;
     const R kHcb = bH * gcb, kHcc = bH * gcc, kHbb = bH * gbb;
-    if constexpr (SIP) {
-        if (hso != nullptr) sip_owner<F, NF, R, TE, MODE>(m0, m1, c, trO, trN, d, hsv, hso, hsr, fs, gac, ca, cb, dtc);
-    }
     // incident face (e+ = e- + 2 E_inc): the E jump is the incident term alone
     const R* inc = (HAS_E && code <= -2 && incp != nullptr && active)
                        ? static_cast<const R*>(incp) + IX(-code - 2) * NF * 3
@@ -470,7 +493,7 @@ __device__ __forceinline__ void flux_face(int m0, int m1, int c, R* trO, const R
         }
     }
     if constexpr (SIP) {
-        if (hsv != nullptr) sip_eflux<F, NF, R, TE>(m0, m1, c, trO, hsv, fs, gac, cE);
+        if (hsv != nullptr) sip_eflux<F, NF, R, TE, MC>(m0, m1, c, trO, hsv, fs, gac, cE);
     }
 }
 
@@ -793,10 +816,10 @@ stage_kernel(const StageParams prm) {
             }
             const R ca = coef(prm.a, prm.a_f), cb = coef(prm.b, prm.b_f), dtc = coef(prm.dt, prm.dt_f);
             switch (f) {
-                case 0: flux_face<0, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
-                case 1: flux_face<1, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
-                case 2: flux_face<2, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
-                default: flux_face<3, NF, R, TE, MODE, IX, SIP>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
+                case 0: flux_face<0, NF, R, TE, MODE, IX, SIP, (NF + CHUNKS - 1) / CHUNKS>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
+                case 1: flux_face<1, NF, R, TE, MODE, IX, SIP, (NF + CHUNKS - 1) / CHUNKS>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
+                case 2: flux_face<2, NF, R, TE, MODE, IX, SIP, (NF + CHUNKS - 1) / CHUNKS>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
+                default: flux_face<3, NF, R, TE, MODE, IX, SIP, (NF + CHUNKS - 1) / CHUNKS>(m0, m1, c, trO, trN, fg, gm, eg, jp, C, col, active, fcode, prm.inc, hsv, hso, hsr, fs, ga + c, ca, cb, dtc); break;
             }
         }
     }
