@@ -171,6 +171,7 @@ struct dgm_plan {
     double sip_alpha = 0.0;          // 0: off
     int64_t n_facets = 0;            // interior facets
     size_t off_sfid = 0;             // [4][K] int32: (facet << 1) | owner, or -1
+    size_t off_fcp = 0;              // [FC_ROWS][K] precomputed face constants (plan precision)
     std::vector<int32_t> sfid_host;
     void* hs[2] = {nullptr, nullptr};
     void* hs_res = nullptr;
@@ -406,6 +407,8 @@ static int plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt
     P->nbr_plain = P->mesh.nbr;
     P->off_sfid = off;   // facet codes of the interior penalty
     off = align256(off + sizeof(int32_t) * 4 * K);
+    P->off_fcp = off;    // precomputed face constants of the stage kernels
+    off = align256(off + size_t(kt->real_size) * FC_ROWS * K);
     P->bytes_geom = off;
     P->k_active = K;
     P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
@@ -472,6 +475,10 @@ __global__ void face_table_kernel(const double* __restrict__ geo, const int32_t*
     }
 }
 
+static void stage_params(dgm_plan* P, StageParams& prm);
+
+// The per-face neighbour table and, from it, the stage kernels' precomputed
+// face constants (after binding, and whenever materials or boundary codes change).
 static int build_face_table(dgm_plan* P) {
     const int64_t K = P->mesh.K;
     if (K == 0) return DGM_OK;
@@ -481,7 +488,14 @@ static int build_face_table(dgm_plan* P) {
         reinterpret_cast<const int32_t*>(P->geom + P->off_nbr), K,
         reinterpret_cast<double*>(P->geom + P->off_fnb), reinterpret_cast<float*>(P->geom + P->off_fnb32));
     const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "face table");
+    if (e != cudaSuccess) return cuda_fail(e, "face table");
+    if (P->mixed) return DGM_OK;   // the mixed-order kernel forms its face terms itself
+    StageParams prm;
+    stage_params(P, prm);
+    const bool sip = P->sip_alpha > 0.0;
+    prm.sfid = sip ? reinterpret_cast<const int32_t*>(P->geom + P->off_sfid) : nullptr;
+    const int rc = launch_face_consts(prm, P->kt->real_size, sip, P->geom + P->off_fcp, P->stream);
+    return rc ? fail(rc, "face constants") : DGM_OK;
 }
 
 int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, void* aux0,
@@ -586,6 +600,7 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.inc = P->n_inc > 0 ? static_cast<const void*>(P->geom + P->off_incv) : nullptr;
     prm.sip_alpha = P->sip_alpha;
     prm.n_facets = P->n_facets;
+    prm.fcp = P->geom + P->off_fcp;
     if (P->sip_alpha > 0.0 && P->hs[0] != nullptr) {
         prm.sfid = reinterpret_cast<const int32_t*>(P->geom + P->off_sfid);
         prm.hs = P->hs[P->cur];
@@ -1003,8 +1018,9 @@ int dgm_set_incident(dgm_plan* P, int64_t n, const int64_t* faces, const dgm_inc
         if (e == cudaSuccess && n > 0)
             e = cudaMemcpyAsync(P->geom + P->off_inc, P->inc_host.data(), sizeof(double) * P->inc_host.size(),
                                 cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "upload incident faces");
+        if (int rc = build_face_table(P)) return rc;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "upload incident faces");
     }
     return DGM_OK;
 }

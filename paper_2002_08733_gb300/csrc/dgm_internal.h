@@ -121,7 +121,14 @@ struct StageParams {
     void* hs_res;
     double sip_alpha;
     int64_t n_facets;
+    const void* fcp;      // precomputed face constants [FC_ROWS][K] (R), see face_consts_kernel
 };
+
+// Rows per element of the precomputed face constants: 4 faces x 16, the
+// metric A^T A (6), A^T (9).
+constexpr int FC_ROWS = 4 * 16 + 6 + 9;
+// Computes them for a plan (dgm_facec.cu); real_size 4 or 8.
+int launch_face_consts(const StageParams& prm, int real_size, bool sip, void* out, void* stream);
 
 // One adjoint stage: lu += dt F_u^T lr, and the material-gradient terms
 // dt lr . (dF/d eps_T, dF/d mu_T) u at the stage input u (per column).

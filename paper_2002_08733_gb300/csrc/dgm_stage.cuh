@@ -179,8 +179,9 @@ __device__ __forceinline__ void face_constants_tab(int f, const R (&ait)[9], R d
     }
 }
 
-// Face constants of the reference-frame flux of face f (written to fc[k * TE])
-// and, when gm is not null, the element's metric A^T A (gm[k * TE]).
+// Face constants of the reference-frame flux of face f (written to fc[k * TE],
+// TE the row stride) and, when gm is not null, the element's metric A^T A
+// (gm[k * TE]).
 //
 // With M = A^-T, the reference traces x of both sides, Q = M^-1 M_n = A^T A_n^-T
 // and the reference jump dx = Q x+ - alpha x- (alpha: 1, or the PEC ghost
@@ -199,11 +200,11 @@ __device__ __forceinline__ void face_constants_tab(int f, const R (&ait)[9], R d
 // e+ = e- + 2 E_inc, h+ = -h-, Z+ = Z-; the E_inc part is added by flux_face).
 // ks_num: alpha / mu_F on the owner side of a penalised interior face, else 0.
 // ga (with gm, face 0 only): the element's A^T, row major, for the penalty.
-template <typename R, int TE, bool SIP>
+template <typename R, bool SIP>
 __device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R det, R epsm, R mum,
                                                    bool has_nbr, const R (&aitn)[9], R zn,
                                                    int upwind, R* fc, R* gm, bool incident,
-                                                   R ks_num, R* ga) {
+                                                   R ks_num, R* ga, int64_t TE) {
     // A^T = det A adj(A^-T), row major
     R at[9];
     at[0] = ait[4] * ait[8] - ait[5] * ait[7];
@@ -260,6 +261,45 @@ __device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R d
         gm[3 * TE] = at[3] * at[3] + at[4] * at[4] + at[5] * at[5];
         gm[4 * TE] = at[3] * at[6] + at[4] * at[7] + at[5] * at[8];
         gm[5 * TE] = at[6] * at[6] + at[7] * at[7] + at[8] * at[8];
+    }
+}
+
+// The stage kernel's face constants, computed once per plan (again when the
+// materials or the boundary codes change) for every element, stride K, in the
+// kernel's precision: rows f FCF + k (the penalty's layout), then the metric
+// A^T A and A^T.  The same function and inputs as a computation inside the
+// stage kernel, so the same bits.
+constexpr int FCF = FGR + 1;
+static_assert(4 * FCF + GM + GA == FC_ROWS, "precomputed face-constant rows");
+template <typename R, bool SIP>
+__global__ void face_consts_kernel(const StageParams prm, R* __restrict__ out) {
+    const int64_t K = prm.K;
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= K) return;
+    const R* gr = static_cast<const R*>(prm.geo_r);
+    R ait[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) ait[k] = gr[int64_t(G_AIT + k) * K + e];
+    const R det = gr[int64_t(G_DET) * K + e];
+    const R epsm = gr[int64_t(G_EPS) * K + e];
+    const R mum = gr[int64_t(G_MU) * K + e];
+    for (int f = 0; f < 4; ++f) {
+        const R* fn = static_cast<const R*>(prm.fnb_r) + int64_t(f * FNB_COUNT) * K + e;
+        const int32_t code = prm.nbr[int64_t(f) * K + e];
+        R aitn[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) aitn[k] = fn[int64_t(FNB_AIT + k) * K];
+        const R zn = fn[int64_t(FNB_Z) * K];
+        R ksn = R(0);   // interior penalty on the facet's owner side: alpha / mu_F
+        if constexpr (SIP) {
+            const int32_t sf = prm.sfid[int64_t(f) * K + e];
+            if (sf >= 0 && (sf & 1)) ksn = R(prm.sip_alpha) / (R(0.5) * (mum + fn[int64_t(FNB_MU) * K]));
+        }
+        face_constants_ref<R, SIP>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
+                                   prm.upwind, out + int64_t(f * FCF) * K + e,
+                                   f == 0 ? out + int64_t(4 * FCF) * K + e : nullptr,
+                                   code <= -2 && prm.inc != nullptr, ksn,
+                                   out + int64_t(4 * FCF + GM) * K + e, K);
     }
 }
 
@@ -626,14 +666,11 @@ stage_kernel(const StageParams prm) {
         nbs[r * TE + c] = !active ? -1 : r < 4 ? prm.nbr[IX(r) * K + e] : prm.sfid[IX(r - 4) * K + e];
 
     // ---- phase 1: tile coefficients, element and face constants --------------
-    // Groups 0..3 compute the face constants of face f = group from the
-    // element's geometry and the per-face neighbour table (one round trip).
-    // The other groups stage the tile's coefficients and element constants,
-    // each thread issuing its loads before its first shared-memory store.
-    // Every group requests the neighbour coefficients of its first phase-2
-    // item, so that the global round trips of the tile overlap.
-    constexpr int FACE_GROUPS = NG > 4 ? 4 : 0;
-    constexpr int LG = NG - FACE_GROUPS;                 // loading groups
+    // Every group loads rows of the tile: the coefficients, the element
+    // constants, and the face constants and metric that the plan precomputed
+    // (face_consts_kernel), each thread's loads in flight together before its
+    // shared-memory stores; every group requests the neighbour coefficients of
+    // its first phase-2 item, so that the global round trips of the tile overlap.
     constexpr int NOWN = 12, NNBR = 24;                 // phase-2 items
     R vn[N];                                            // neighbour coefficients (phase 2)
     auto nbr_item_active = [&](int comp) {
@@ -648,80 +685,51 @@ stage_kernel(const StageParams prm) {
             for (int l = 0; l < N; ++l) dst[l] = u[IX((ni % 6) * N + l) * C + ncol];
         }
     };
-    auto face_consts = [&](int f) {
-        R ait[9], aitn[9];
-        const R* fn = static_cast<const R*>(prm.fnb_r) + IX(f * FNB_COUNT) * K + e;
-        const int32_t code = active ? prm.nbr[IX(f) * K + e] : -1;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) ait[k] = active ? gr[IX(G_AIT + k) * K + e] : R(k % 4 == 0);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) aitn[k] = active ? fn[IX(FNB_AIT + k) * K] : ait[k];
-        const R det = active ? gr[IX(G_DET) * K + e] : R(1);
-        const R epsm = active ? gr[IX(G_EPS) * K + e] : R(1);
-        const R mum = active ? gr[IX(G_MU) * K + e] : R(1);
-        const R zn = active ? fn[IX(FNB_Z) * K] : R(1);
-        // interior penalty on the facet's owner side: alpha / mu_F, mu_F the mean of both sides
-        R ksn = R(0);
-        if constexpr (SIP) {
-            if (active) {
-                const int32_t sf = prm.sfid[IX(f) * K + e];
-                if (sf >= 0 && (sf & 1))
-                    ksn = R(prm.sip_alpha) / (R(0.5) * (mum + fn[IX(FNB_MU) * K]));
+    {
+        // rows q: [0, 6N) coefficients, then EG element constants, 4 FGRT face
+        // constants, GM metric rows and (penalty) GA rows of A^T
+        constexpr int Q0 = 6 * N, Q1 = Q0 + EG, Q2 = Q1 + 4 * FGRT, Q3 = Q2 + GM;
+        constexpr int T1 = Q3 + (SIP ? GA : 0);
+        constexpr int UR = (T1 + NG - 1) / NG;          // rows per thread (at most)
+        constexpr int BATCH = UR < 16 ? UR : 16;        // loads in flight per thread
+        const R* fcp = static_cast<const R*>(prm.fcp);
+        auto load = [&](int q) -> R {
+            if (q < Q0) return active ? u[IX(q) * C + col] : R(0);
+            if (q < Q1) {
+                const int k = q - Q0;
+                return active ? gr[IX(k) * K + e] : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
             }
-        }
-        face_constants_ref<R, TE, SIP>(f, ait, det, epsm, mum, code >= 0 && (code >> 2) < K, aitn, zn,
-                                       prm.upwind, fg + f * FGRT * TE + c, f == 0 ? gm + c : nullptr,
-                                  code <= -2 && prm.inc != nullptr, ksn, ga + c);
-    };
-    // neighbour code of this group's round-0 item, loaded with the other
-    // independent loads so that the dependent gather starts one round trip in
-    const int32_t code0 = (grp < NNBR && active) ? prm.nbr[IX(grp / 6) * K + e] : -1;
-    if (grp < FACE_GROUPS) {
-        face_consts(grp);
-        request_nbr(grp, code0, vn);
-    } else {
-        const int lg = grp - FACE_GROUPS;
-        constexpr int UR = (6 * N + LG - 1) / LG;        // coefficient rows per thread
-        constexpr int ER = (EG + LG - 1) / LG;           // element-constant rows per thread
-        constexpr int BATCH = 16;                        // loads in flight per thread
-        // first batch of tile rows, element constants and the round-0 code in flight together
+            if (q < Q2) {
+                const int f = (q - Q1) / FGRT, k = (q - Q1) % FGRT;
+                return active ? fcp[IX(f * FCF + k) * K + e] : R(0);
+            }
+            if (q < Q3) return active ? fcp[IX(4 * FCF + q - Q2) * K + e] : R(0);
+            return active ? fcp[IX(4 * FCF + GM + q - Q3) * K + e] : R(0);
+        };
+        auto store = [&](int q, R v) {
+            if (q < Q0) us[q * TE + c] = v;
+            else if (q < Q1) eg[(q - Q0) * TE + c] = v;
+            else if (q < Q2) fg[(q - Q1) * TE + c] = v;
+            else if (q < Q3) gm[(q - Q2) * TE + c] = v;
+            else ga[(q - Q3) * TE + c] = v;
+        };
+        // neighbour code of this group's round-0 item, with the first batch
+        const int32_t code0 = (grp < NNBR && active) ? prm.nbr[IX(grp / 6) * K + e] : -1;
         R tmp[BATCH];
 #pragma unroll
-        for (int i = 0; i < BATCH; ++i) {
-            const int r = lg + i * LG;
-            tmp[i] = (i < UR && r < 6 * N && active) ? u[IX(r) * C + col] : R(0);
-        }
-        R tmpe[ER];
-#pragma unroll
-        for (int i = 0; i < ER; ++i) {
-            const int k = lg + i * LG;
-            tmpe[i] = (k < EG && active) ? gr[IX(k) * K + e]
-                                         : R(k == G_DET || k == G_EPS || k == G_MU ? 1 : 0);
-        }
-        request_nbr(grp, code0, vn);
-#pragma unroll
         for (int i0 = 0; i0 < UR; i0 += BATCH) {
-            if (i0 > 0) {
-#pragma unroll
-                for (int i = 0; i < BATCH; ++i) {
-                    const int r = lg + (i0 + i) * LG;
-                    tmp[i] = (i0 + i < UR && r < 6 * N && active) ? u[IX(r) * C + col] : R(0);
-                }
-            }
 #pragma unroll
             for (int i = 0; i < BATCH; ++i) {
-                const int r = lg + (i0 + i) * LG;
-                if (i0 + i < UR && r < 6 * N) us[r * TE + c] = tmp[i];
+                const int q = grp + (i0 + i) * NG;
+                tmp[i] = (i0 + i < UR && q < T1) ? load(q) : R(0);
+            }
+            if (i0 == 0) request_nbr(grp, code0, vn);
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int q = grp + (i0 + i) * NG;
+                if (i0 + i < UR && q < T1) store(q, tmp[i]);
             }
         }
-#pragma unroll
-        for (int i = 0; i < ER; ++i) {
-            const int k = lg + i * LG;
-            if (k < EG) eg[k * TE + c] = tmpe[i];
-        }
-    }
-    if (FACE_GROUPS == 0) {
-        for (int f = grp; f < 4; f += NG) face_consts(f);
     }
     __syncthreads();
 
