@@ -691,7 +691,7 @@ stage_kernel(const StageParams prm) {
         constexpr int Q0 = 6 * N, Q1 = Q0 + EG, Q2 = Q1 + 4 * FGRT, Q3 = Q2 + GM;
         constexpr int T1 = Q3 + (SIP ? GA : 0);
         constexpr int UR = (T1 + NG - 1) / NG;          // rows per thread (at most)
-        constexpr int BATCH = UR < 16 ? UR : 16;        // loads in flight per thread
+        constexpr int BATCH = UR < 24 ? UR : 16;        // loads in flight per thread (one batch when it fits)
         const R* fcp = static_cast<const R*>(prm.fcp);
         auto load = [&](int q) -> R {
             if (q < Q0) return active ? u[IX(q) * C + col] : R(0);
