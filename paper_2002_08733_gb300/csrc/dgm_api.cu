@@ -52,8 +52,9 @@ constexpr int ENERGY_THREADS = 256;
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// incident plane-wave table: header values, values per face, largest face rule
-constexpr int INC_HDR = 8, INC_FACE = 6, INC_MAXQ = 128;
+// incident plane-wave table: header values, values per face, largest face rule,
+// stage slots of the jump terms
+constexpr int INC_HDR = 8, INC_FACE = 6, INC_MAXQ = 128, INC_SLOTS = 5;
 static_assert((PMAX + 6) * (PMAX + 6) <= INC_MAXQ, "face rule larger than a warp's four rounds");
 
 // Bytes of the tensor-core variant's operator image for degree p (0: no variant).
@@ -176,6 +177,11 @@ struct dgm_plan {
     void* hs[2] = {nullptr, nullptr};
     void* hs_res = nullptr;
 };
+
+// bytes of one stage slot of the incident jump terms (every boundary face)
+static size_t inc_slot_bytes(const dgm_plan* P) {
+    return size_t(P->kt->real_size) * 3 * P->NF * P->n_bfaces;
+}
 
 static thread_local std::string g_err;
 
@@ -401,8 +407,8 @@ static int plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt
     if (!mixed) {
         off = align256(off + sizeof(double) * (INC_HDR + size_t(P->inc_nq) * (2 + P->NF) +
                                                size_t(INC_FACE) * P->n_bfaces));
-        P->off_incv = off;
-        off = align256(off + size_t(kt->real_size) * 3 * P->NF * P->n_bfaces);
+        P->off_incv = off;   // jump terms: one slot per LSRK stage of a step
+        off = align256(off + INC_SLOTS * inc_slot_bytes(P));
     }
     P->nbr_plain = P->mesh.nbr;
     P->off_sfid = off;   // facet codes of the interior penalty
@@ -632,8 +638,14 @@ static void sip_stage(const dgm_plan* P, StageParams& prm) {
 // The delay x = t - t0 - tau_q is formed in FP64 (t may be large against the
 // pulse width); the pulse and the sums run in the plan's precision (an FP32
 // plan rounds the jump terms to FP32 anyway).
+struct IncTimes {
+    double t[INC_SLOTS];
+};
 template <typename R>
-__global__ void incident_eval(const double* __restrict__ tab, int NF, double t, R* __restrict__ out) {
+__global__ void incident_eval(const double* __restrict__ tab, int NF, IncTimes ts, int64_t slot,
+                              R* __restrict__ out) {
+    const double t = ts.t[blockIdx.y];
+    out += int64_t(blockIdx.y) * slot;
     const int lane = threadIdx.x & 31;
     const int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nf = int64_t(tab[4]);
@@ -668,19 +680,34 @@ __global__ void incident_eval(const double* __restrict__ tab, int NF, double t, 
     }
 }
 
-// A stage launch; with incident faces, their jump terms at the stage time first.
-static int launch_stage(dgm_plan* P, StageParams& prm, int mode, cudaStream_t st) {
+// The incident jump terms at n (<= INC_SLOTS) times, into slots 0 .. n-1: one
+// launch for the five stages of an LSRK step.
+static int incident_eval_times(dgm_plan* P, const double* t, int n, cudaStream_t st) {
+    IncTimes ts{};
+    for (int k = 0; k < n; ++k) ts.t[k] = t[k];
+    const double* tab = reinterpret_cast<const double*>(P->geom + P->off_inc);
+    const dim3 grid(unsigned((P->n_inc + 3) / 4), unsigned(n));
+    const int64_t slot = int64_t(P->n_inc) * P->NF * 3;   // reals per slot in use
+    if (P->kt->real_size == 8)
+        incident_eval<double><<<grid, 128, 0, st>>>(tab, P->NF, ts, slot,
+                                                     reinterpret_cast<double*>(P->geom + P->off_incv));
+    else
+        incident_eval<float><<<grid, 128, 0, st>>>(tab, P->NF, ts, slot,
+                                                    reinterpret_cast<float*>(P->geom + P->off_incv));
+    return cudaGetLastError() == cudaSuccess ? DGM_OK : DGM_ECUDA;
+}
+
+// A stage launch.  With incident faces the kernel reads the jump terms of
+// `slot`, evaluated by the caller for this stage's time; slot < 0 evaluates
+// them here at prm.t (into slot 0).
+static int launch_stage(dgm_plan* P, StageParams& prm, int mode, cudaStream_t st, int slot = -1) {
     if (P->n_inc > 0) {
-        const double* tab = reinterpret_cast<const double*>(P->geom + P->off_inc);
-        const unsigned grid = unsigned((P->n_inc + 3) / 4);
-        if (P->kt->real_size == 8)
-            incident_eval<double><<<grid, 128, 0, st>>>(tab, P->NF, prm.t,
-                                                         reinterpret_cast<double*>(P->geom + P->off_incv));
-        else
-            incident_eval<float><<<grid, 128, 0, st>>>(tab, P->NF, prm.t,
-                                                        reinterpret_cast<float*>(P->geom + P->off_incv));
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return DGM_ECUDA;
+        if (slot < 0) {
+            if (int rc = incident_eval_times(P, &prm.t, 1, st)) return rc;
+            slot = 0;
+        }
+        prm.inc = P->geom + P->off_incv +
+                  size_t(slot) * size_t(P->n_inc) * P->NF * 3 * size_t(P->kt->real_size);
     }
     return P->kt->launch_stage(prm, mode, st);
 }
@@ -867,6 +894,11 @@ int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
     for (int64_t n = 0; n < n_steps; ++n) {
         const double t = t0 + double(n) * dt;
         if (P->opt.integrator == DGM_LSRK4) {
+            if (P->n_inc > 0) {   // the step's five stage times in one launch
+                double ts[5];
+                for (int k = 0; k < 5; ++k) ts[k] = t + LSRK_C[k] * dt;
+                if (int rc = incident_eval_times(P, ts, 5, P->stream)) return fail(rc, "incident launch failed");
+            }
             for (int k = 0; k < 5; ++k) {
                 prm.u = P->fields[P->cur];
                 prm.u_out = P->fields[1 - P->cur];
@@ -878,7 +910,7 @@ int dgm_advance(dgm_plan* P, int64_t n_steps, double t0) {
                 prm.a = LSRK_A[k];
                 prm.b = LSRK_B[k];
                 sip_stage(P, prm);
-                int rc = launch_stage(P, prm, MODE_LSRK, P->stream);
+                int rc = launch_stage(P, prm, MODE_LSRK, P->stream, k);
                 if (rc) return fail(rc, "stage kernel launch failed");
                 P->cur = 1 - P->cur;
             }
