@@ -26,10 +26,11 @@
 // two components.
 //
 // Phases (separated by __syncthreads):
-//   1 load the tile's coefficients into shared memory, element geometry
+//   1 load the tile's coefficients, element constants and the precomputed
+//     face constants (neighbour map, flux coefficients; face_consts_kernel)
+//     into shared memory
 //   2 own traces (4 faces x 6 components) from shared memory, neighbour traces
-//     from global memory (the neighbour's coefficients are usually L2 hits),
-//     face constants (normal, neighbour map, flux coefficients)
+//     from global memory (the neighbour's coefficients are usually L2 hits)
 //   3 numerical flux per (face, face mode) in the reference frame
 //   4 right-hand side per component: volume curl + lift (+ source)
 //   5 3x3 mass-block inverse, PML terms, and the stage update
