@@ -832,15 +832,12 @@ stage_kernel(const StageParams prm) {
             }
         }
     }
-    __syncthreads();
-
-    // ---- phase 4: volume curl + lift per (component, row part) -----------------
-    R* rh = trN;   // [6][N][TE], the neighbour traces are dead now
     // Phase 5 works per (field, row part): one item updates the three
     // components of a field on its rows, so that the 3x3 mass block is applied
     // once per row and each right-hand-side value is read once.  The LSRK
-    // residual rows of that item are requested now, so that their latency
-    // overlaps the phase-4 arithmetic.
+    // residual rows of that item are requested as soon as the thread's flux
+    // item is done, so that their latency overlaps the wait at the phase-3
+    // barrier and the phase-4 arithmetic.
     constexpr int NP5 = (NG / 2 < N ? NG / 2 : N) > 0 ? (NG / 2 < N ? NG / 2 : N) : 1;   // row parts per field
     constexpr int RP5 = (N + NP5 - 1) / NP5;          // rows per part (at most)
     constexpr bool P5_EVEN = (N % NP5) == 0;          // every part has exactly RP5 rows
@@ -857,6 +854,10 @@ stage_kernel(const StageParams prm) {
             for (int i = 0; i < RP5; ++i)
                 resv[k][i] = (load && (P5_EVEN || lo + i < hi)) ? res[IX((fb + k) * N + lo + i) * C + col] : R(0);
     }
+    __syncthreads();
+
+    // ---- phase 4: volume curl + lift per (component, row part) -----------------
+    R* rh = trN;   // [6][N][TE], the neighbour traces are dead now
     // tensor-core variant: per row (field F, column c) stage A_swap = +-s_T times
     // the other field and the pulled-back fluxes A_g of F's three components in
     // tensor memory (TF32 hi/lo), then one thread issues the MMAs
