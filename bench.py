@@ -190,11 +190,15 @@ def run_gpu(args, precision, steps, warmup, world, rank):
         g.set_variant(args.variant)
         if args.tile_groups is not None:
             g.set_tile_groups(args.tile_groups)
-        tuned = {"variant": int(args.variant), "forced": True, "tile_groups": g.tile_groups()}
+        if args.tile_loads is not None:
+            g.set_tile_loads(args.tile_loads == "per_thread")
+        tuned = {"variant": int(args.variant), "forced": True, "tile_groups": g.tile_groups(),
+                 "bulk_tile_loads": g.bulk_tile_loads()}
     elif precision == "fp32":
         v, ms = g.autotune()
         tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms],
-                 "variants": VARIANT_NAMES[:len(ms)], "tile_groups": g.tile_groups()}
+                 "variants": VARIANT_NAMES[:len(ms)], "tile_groups": g.tile_groups(),
+                 "bulk_tile_loads": g.bulk_tile_loads()}
     t = 0.0
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -227,7 +231,8 @@ def run_gpu(args, precision, steps, warmup, world, rank):
     return out
 
 
-def run_pml(precision, steps, warmup, n=40, integrator="lsrk4", variant=None, groups=None):
+def run_pml(precision, steps, warmup, n=40, integrator="lsrk4", variant=None, groups=None,
+            loads=None):
     """Dipole-in-PML workload: [-1,1]^3 on an n^3 Kuhn grid (384,000 tets at n=40),
     p=4, PML 0.25 thick with quadratic profile and sigma_max=40, z-directed
     dipole, starting from rest; upwind flux with LSRK4 or, with
@@ -249,11 +254,15 @@ def run_pml(precision, steps, warmup, n=40, integrator="lsrk4", variant=None, gr
         g.set_variant(variant)     # profiling runs: the shape the autotuner picks, pinned
         if groups is not None:
             g.set_tile_groups(groups)
-        tuned = {"variant": int(variant), "forced": True, "tile_groups": g.tile_groups()}
+        if loads is not None:
+            g.set_tile_loads(loads == "per_thread")
+        tuned = {"variant": int(variant), "forced": True, "tile_groups": g.tile_groups(),
+                 "bulk_tile_loads": g.bulk_tile_loads()}
     elif precision == "fp32" and integrator == "lsrk4":   # tile shape (state untouched)
         v, ms_v = g.autotune()
         tuned = {"variant": int(v), "ms_per_launch": [float(x) for x in ms_v],
-                 "tile_groups": g.tile_groups()}
+                 "tile_groups": g.tile_groups(),
+                 "bulk_tile_loads": g.bulk_tile_loads()}
     t = 0.0
     if integrator == "leapfrog":
         g.leapfrog_start(0.0)
@@ -588,20 +597,21 @@ def run_adjoint(steps, n=24):
 TRAFFIC_PROFILE = "stage_kernel_full_jittered_sphere_n28_p3_fp32.md"
 
 
-def profiled_traffic(path, variant, groups, columns):
+def profiled_traffic(path, variant, groups, columns, loads="bulk"):
     """DRAM bytes of one stage launch from the committed ncu summary: its line
-    `traffic_bytes_per_element_stage variant=V tile_groups=G: B` for the tile
-    shape and tile order this run uses, times the columns; None when the
-    summary has no line for them (counters of another shape or order say
-    nothing about this one)."""
+    `traffic_bytes_per_element_stage variant=V tile_groups=G loads=L: B` for
+    the tile shape, tile order and phase-1 load path (bulk copies or
+    per-thread loads) this run uses, times the columns; None when the summary
+    has no line for them (counters of another kernel configuration say nothing
+    about this one)."""
     import re
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    for m in re.finditer(r"traffic_bytes_per_element_stage variant=(\d+) tile_groups=(\d+):"
-                         r"\s*(\d+)", txt):
-        if int(m.group(1)) == variant and int(m.group(2)) == groups:
-            return int(m.group(3)) * columns
+    for m in re.finditer(r"traffic_bytes_per_element_stage variant=(\d+) tile_groups=(\d+)"
+                         r" loads=(\w+):\s*(\d+)", txt):
+        if int(m.group(1)) == variant and int(m.group(2)) == groups and m.group(3) == loads:
+            return int(m.group(4)) * columns
     return None
 
 
@@ -761,6 +771,9 @@ def main():
                          "(profiling runs: the autotuner's timings are distorted under ncu)")
     ap.add_argument("--tile-groups", type=int, default=None,
                     help="with --variant: force the FP32 tile visiting order (default: plain order)")
+    ap.add_argument("--tile-loads", choices=["bulk", "per_thread"], default=None,
+                    help="with --variant: force the stage kernel's phase-1 load path (default: "
+                         "bulk copies where the plan allows them)")
     ap.add_argument("--adjoint-steps", type=int, default=1500,
                     help="steps of the inverse problem (1500, its stated step count)")
     ap.add_argument("--pml-steps", type=int, default=20)
@@ -833,7 +846,7 @@ def main():
         return
     if args.only == "pml":
         r = run_pml("fp32", args.pml_steps, args.warmup, n=args.pml_n, variant=args.variant,
-                    groups=args.tile_groups)
+                    groups=args.tile_groups, loads=args.tile_loads)
         r.pop("_final")
         if rank == 0:
             print(json.dumps({"profile_run": "pml", **r}))
@@ -868,8 +881,9 @@ def main():
     # figure for this tile shape and tile order, per element-stage times columns
     chosen = (r32["tuned"] or {}).get("variant", 0)
     groups = (r32["tuned"] or {}).get("tile_groups", 1)
+    loads = "bulk" if (r32["tuned"] or {}).get("bulk_tile_loads", False) else "per_thread"
     traffic = profiled_traffic(os.path.join(ROOT, "profiles", TRAFFIC_PROFILE), chosen, groups,
-                               r32["K"] * r32["S"])
+                               r32["K"] * r32["S"], loads)
     line = {
         "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps,

@@ -222,7 +222,10 @@ int dgm_adjoint(dgm_plan* plan, int64_t n_steps, double t0, const double* drecor
  * CTA) of the LSRK4 stage kernel on the plan's current state, `reps` launches
  * each, and keeps the fastest for later dgm_advance / dgm_batch_create calls;
  * then times the tile visiting orders of dgm_set_tile_groups for that shape
- * (at least ten launches each).  The plan's state is only read.  An LSRK4
+ * (at least ten launches each) and, where the plan has the phase-1 bulk copies
+ * of dgm_set_tile_loads, those against per-thread loads (each twice, the
+ * faster of its two times), keeping per-thread loads only when they are
+ * faster.  The plan's state is only read.  An LSRK4
  * plan is timed on stage sequences as dgm_advance runs them: the first launch
  * reads the state and writes `workspace`, later ones alternate between
  * `workspace` and the plan's second field (and auxiliary) buffer, which hold
@@ -241,6 +244,21 @@ int dgm_set_variant(dgm_plan* plan, int32_t variant);
  * always, to check that path on problems of any size.  Results are the same
  * either way.  DGM_EINVAL for other values. */
 int dgm_set_index64(dgm_plan* plan, int32_t force);
+/* How the single-column stage kernels bring a tile's coefficients, element
+ * constants and face constants into shared memory.  Where the plan allows it
+ * (one column per element, S = 1; rows of the field and table buffers on
+ * 16-byte boundaries, i.e. K a multiple of 4 in FP32 and of 2 in FP64; the
+ * stage reads one of the two bound field buffers) dgm_bind builds tensor maps
+ * and phase 1 moves the tile with a few tiled bulk copies (TMA) issued by one
+ * thread; otherwise every thread loads and stores its share of rows.
+ * per_thread = 1 forces the per-thread loads, 0 (the default) restores the
+ * automatic choice; the results are the same bits either way.  DGM_EINVAL for
+ * other values.  dgm_get_tile_loads sets *bulk to 1 when the next stages of a
+ * bound plan use the bulk copies, else 0.  A bulk copy that has not completed
+ * within 0.5 s leaves its tile unwritten and latches DGM_ETIMEOUT in the
+ * device status word (dgm_status_check). */
+int dgm_set_tile_loads(dgm_plan* plan, int32_t per_thread);
+int dgm_get_tile_loads(const dgm_plan* plan, int32_t* bulk);
 /* Order in which the stage and adjoint kernels visit their column tiles:
  * with groups = G > 1 (and a tile count that G divides) consecutive CTAs
  * take tiles from G equal segments of the columns in turn, which keeps the

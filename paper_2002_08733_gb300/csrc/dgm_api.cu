@@ -1,6 +1,8 @@
 // C ABI of the dgmax library: plans, binding of caller-owned device memory,
 // the time-stepping drivers (LSRK4 stages, leapfrog half steps), the FP64
 // energy reduction, point sources and L2 projection of initial values.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -176,6 +178,11 @@ struct dgm_plan {
     std::vector<int32_t> sfid_host;
     void* hs[2] = {nullptr, nullptr};
     void* hs_res = nullptr;
+    // tensor maps of the stage kernels' phase-1 bulk copies (built at bind)
+    size_t off_tmap = 0;             // TMAP_SETS x TMAP_COUNT maps of TMAP_BYTES
+    bool tmaps_ok = false;           // built: one column per element, aligned rows
+    int tile_loads = 0;              // dgm_set_tile_loads: 1 forces per-thread loads
+    std::vector<CUtensorMap> tmap_host;
 };
 
 // bytes of one stage slot of the incident jump terms (every boundary face)
@@ -415,6 +422,8 @@ static int plan_create(dgm_plan** out, int64_t nv, const double* xyz, int64_t nt
     off = align256(off + sizeof(int32_t) * 4 * K);
     P->off_fcp = off;    // precomputed face constants of the stage kernels
     off = align256(off + size_t(kt->real_size) * FC_ROWS * K);
+    P->off_tmap = off;   // tensor maps of the phase-1 bulk copies
+    off = align256(off + size_t(TMAP_SETS) * TMAP_COUNT * TMAP_BYTES);
     P->bytes_geom = off;
     P->k_active = K;
     P->src_host.assign(size_t(Sc) * (SRC_HDR + 3 * P->N), 0.0);
@@ -485,6 +494,128 @@ static void stage_params(dgm_plan* P, StageParams& prm);
 
 // The per-face neighbour table and, from it, the stage kernels' precomputed
 // face constants (after binding, and whenever materials or boundary codes change).
+// The driver's tensor-map encoder, looked up once through the runtime (null
+// when the driver does not provide it; the stage kernels then load per thread).
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        (void)cudaGetLastError();   // a failed lookup must not surface at the next launch check
+    });
+    return fn;
+}
+
+// Tensor maps of the stage kernels' phase-1 bulk copies (TmapIndex), for the
+// bound field buffers, the element constants and the face-constant table.
+// Built when each element has one column (S = 1: a tile's columns are
+// consecutive elements in every table) and every row starts on a 16-byte
+// boundary; otherwise, or when the driver has no encoder, the kernels keep
+// their per-thread loads.  The maps hold addresses only, so they stay valid
+// until the next bind.
+static_assert(sizeof(CUtensorMap) == TMAP_BYTES, "tensor-map slot size");
+
+// tile width of a tensor-map set: rows of 128 bytes (set 0), 16 FP32 columns
+// (set 1, FP32 plans only); 0 when the set does not exist for the plan
+static cuuint32_t tmap_tile(const dgm_plan* P, int set) {
+    const int rs = P->kt->real_size;
+    return set == 0 ? cuuint32_t(128 / rs) : (rs == 4 ? 16u : 0u);
+}
+
+static bool tmap_encode(const dgm_plan* P, CUtensorMap* out, void* base, cuuint32_t rank,
+                        const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        P->kt->real_size == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return encode != nullptr &&
+           encode(out, dt, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the field-shaped buffer `base` ([6][N][C], C = K) into map `slot` of every
+// set of the host copy; false if a buffer is misaligned or the encoder refuses
+static bool tmap_fields(dgm_plan* P, void* base, int slot) {
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+    const cuuint64_t row = cuuint64_t(P->mesh.K) * cuuint64_t(P->kt->real_size);
+    const cuuint64_t dims[3] = {cuuint64_t(P->mesh.K), cuuint64_t(P->N), 6};
+    const cuuint64_t str[2] = {row, row * cuuint64_t(P->N)};
+    for (int set = 0; set < TMAP_SETS; ++set) {
+        const cuuint32_t te = tmap_tile(P, set);
+        if (te == 0) continue;
+        const cuuint32_t box[3] = {te, cuuint32_t(P->N), 6};
+        if (!tmap_encode(P, &P->tmap_host[size_t(set) * TMAP_COUNT + slot], base, 3, dims, str, box))
+            return false;
+    }
+    return true;
+}
+
+// upload the host copy of the maps (on the plan's stream; the host copy lives
+// in the plan, so it outlasts the copy)
+static int tmap_upload(dgm_plan* P) {
+    cudaError_t e = cudaMemcpyAsync(P->geom + P->off_tmap, P->tmap_host.data(),
+                                    P->tmap_host.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                                    P->stream);
+    return e == cudaSuccess ? DGM_OK : cuda_fail(e, "upload tensor maps");
+}
+
+// Tensor maps of the stage kernels' phase-1 bulk copies (TmapIndex), for the
+// bound field buffers, the element constants and the face-constant table.
+// Built when each element has one column (S = 1: a tile's columns are
+// consecutive elements in every table) and every row starts on a 16-byte
+// boundary; otherwise, or when the driver has no encoder, the kernels keep
+// their per-thread loads.  The maps hold addresses only, so they stay valid
+// until the next bind.
+static int build_tmaps(dgm_plan* P) {
+    P->tmaps_ok = false;
+    const int rs = P->kt->real_size;
+    const int64_t K = P->mesh.K;
+    if (P->opt.n_columns != 1 || K <= 0 || (K * rs) % 16 != 0 || K >= (int64_t(1) << 31)) return DGM_OK;
+    if (tmap_encoder() == nullptr) return DGM_OK;
+    P->tmap_host.assign(size_t(TMAP_SETS) * TMAP_COUNT, CUtensorMap{});
+    for (int b = 0; b < 2; ++b)
+        if (P->fields[b] != nullptr && !tmap_fields(P, P->fields[b], TM_U0 + b)) return DGM_OK;
+    const cuuint64_t Ke = cuuint64_t(K), row = cuuint64_t(K) * cuuint64_t(rs);   // row stride in bytes
+    unsigned char* geo = P->geom + (rs == 8 ? P->off_geo : P->off_geo32);
+    unsigned char* fcp = P->geom + P->off_fcp;
+    for (int set = 0; set < TMAP_SETS; ++set) {
+        const cuuint32_t te = tmap_tile(P, set);
+        if (te == 0) continue;
+        CUtensorMap* m = P->tmap_host.data() + size_t(set) * TMAP_COUNT;
+        bool ok = true;
+        {   // element constants [G_COUNT][K]
+            const cuuint64_t dims[2] = {Ke, cuuint64_t(G_COUNT)};
+            const cuuint32_t box[2] = {te, cuuint32_t(TM_ROWS_EG)};
+            ok = ok && tmap_encode(P, &m[TM_GEO], geo, 2, dims, &row, box);
+        }
+        {   // face constants [4][16][K]: 15 rows per face, 16 with the penalty
+            const cuuint64_t dims[3] = {Ke, cuuint64_t(TM_ROWS_FACE), 4};
+            const cuuint64_t str[2] = {row, row * cuuint64_t(TM_ROWS_FACE)};
+            const cuuint32_t box[3] = {te, cuuint32_t(TM_ROWS_FC), 4};
+            const cuuint32_t boxs[3] = {te, cuuint32_t(TM_ROWS_FACE), 4};
+            ok = ok && tmap_encode(P, &m[TM_FC], fcp, 3, dims, str, box);
+            ok = ok && tmap_encode(P, &m[TM_FCS], fcp, 3, dims, str, boxs);
+        }
+        {   // metric (and A^T) rows of the table [FC_ROWS][K], from row 4 * 16
+            const cuuint64_t dims[2] = {Ke, cuuint64_t(FC_ROWS)};
+            const cuuint32_t box[2] = {te, cuuint32_t(TM_ROWS_GM)};
+            const cuuint32_t boxs[2] = {te, cuuint32_t(TM_ROWS_GM + TM_ROWS_GA)};
+            ok = ok && tmap_encode(P, &m[TM_GM], fcp, 2, dims, &row, box);
+            ok = ok && tmap_encode(P, &m[TM_GMGA], fcp, 2, dims, &row, boxs);
+        }
+        if (!ok) return DGM_OK;   // a shape the encoder refuses: per-thread loads
+    }
+    if (int rc = tmap_upload(P)) return rc;
+    P->tmaps_ok = true;
+    return DGM_OK;
+}
+
 static int build_face_table(dgm_plan* P) {
     const int64_t K = P->mesh.K;
     if (K == 0) return DGM_OK;
@@ -575,6 +706,7 @@ int dgm_bind(dgm_plan* P, void* geom, void* fields0, void* fields1, void* res, v
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "upload facet codes");
     if (int rc = build_face_table(P)) return rc;
+    if (int rc = build_tmaps(P)) return rc;
     // the host copies above are pageable: finish them before the host vectors can change
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "bind sync");
     P->bound = true;
@@ -607,6 +739,12 @@ static void stage_params(dgm_plan* P, StageParams& prm) {
     prm.sip_alpha = P->sip_alpha;
     prm.n_facets = P->n_facets;
     prm.fcp = P->geom + P->off_fcp;
+    if (P->tmaps_ok && P->tile_loads == 0) {   // phase-1 bulk copies (the launchers pick the map)
+        prm.tmaps = P->geom + P->off_tmap;
+        prm.tm_f0 = P->fields[0];
+        prm.tm_f1 = P->fields[1];
+    }
+    prm.tm_u = -1;
     if (P->sip_alpha > 0.0 && P->hs[0] != nullptr) {
         prm.sfid = reinterpret_cast<const int32_t*>(P->geom + P->off_sfid);
         prm.hs = P->hs[P->cur];
@@ -1815,6 +1953,16 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
     const size_t fb = align256(info.bytes_fields), ab = align256(info.bytes_aux);
     StageParams prm;
     stage_params(P, prm);
+    // Phase-1 bulk copies where the plan has tensor maps: a map of the
+    // workspace's first field buffer too, so that every timed launch takes
+    // them; the last stage below times them against per-thread loads.
+    const bool bulk_ok = P->tmaps_ok && tmap_fields(P, ws, TM_UW) && tmap_upload(P) == DGM_OK;
+    if (bulk_ok) {
+        prm.tmaps = P->geom + P->off_tmap;
+        prm.tm_f0 = P->fields[0];
+        prm.tm_f1 = P->fields[1];
+        prm.tm_fw = ws;
+    }
     // An LSRK4 plan is timed on stage sequences as the time loop runs them:
     // the first (untimed) launch reads the state and writes workspace buffer
     // 0, later launches ping-pong between that buffer and the plan's second
@@ -1901,11 +2049,28 @@ extern "C" int dgm_autotune(dgm_plan* P, void* workspace, int32_t reps, float* m
             if (g_ms[bi] < 0.99f * g_ms[0]) best_g = cand[bi];
         }
     }
+    // then bulk copies against per-thread loads for that shape and order, each
+    // timed twice in turn (the faster of its two): per-thread loads only when
+    // they are faster
+    int tile_loads = P->tile_loads;
+    if (rc == DGM_OK && bulk_ok) {
+        prm.tile_groups = best_g;
+        float t_ms[2] = {1e30f, 1e30f};
+        for (int r = 0; r < 4 && rc == DGM_OK; ++r) {
+            const int pt = r % 2;
+            prm.tmaps = pt ? nullptr : static_cast<const void*>(P->geom + P->off_tmap);
+            float ms = 0.f;
+            rc = time_it(reps < 10 ? 10 : reps, &ms);
+            t_ms[pt] = std::min(t_ms[pt], ms);
+        }
+        if (rc == DGM_OK) tile_loads = t_ms[1] < t_ms[0] ? 1 : 0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != DGM_OK) return rc;
     P->variant = best;
     P->tile_groups = best_g;
+    P->tile_loads = tile_loads;
     return DGM_OK;
 }
 
@@ -1936,6 +2101,19 @@ extern "C" int dgm_set_variant(dgm_plan* P, int32_t v) {
         return fail(DGM_EUNSUP, "this stage variant has neither incident faces nor the penalty "
                                 "(the penalty runs in the default shape)");
     P->variant = v;
+    return DGM_OK;
+}
+
+extern "C" int dgm_set_tile_loads(dgm_plan* P, int32_t per_thread) {
+    if (!P) return fail(DGM_EINVAL, "null plan");
+    if (per_thread != 0 && per_thread != 1) return fail(DGM_EINVAL, "per_thread must be 0 or 1");
+    P->tile_loads = per_thread;
+    return DGM_OK;
+}
+
+extern "C" int dgm_get_tile_loads(const dgm_plan* P, int32_t* bulk) {
+    if (!P || !bulk) return fail(DGM_EINVAL, "null argument");
+    *bulk = (P->bound && P->tmaps_ok && P->tile_loads == 0) ? 1 : 0;
     return DGM_OK;
 }
 

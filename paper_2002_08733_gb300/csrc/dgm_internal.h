@@ -122,7 +122,36 @@ struct StageParams {
     double sip_alpha;
     int64_t n_facets;
     const void* fcp;      // precomputed face constants [FC_ROWS][K] (R), see face_consts_kernel
+    // Tiled bulk copies of the stage kernel's phase 1 (null: per-thread loads).
+    // tmaps: the plan's tensor maps in device memory, TMAP_SETS sets of TMAP_COUNT
+    // (one set per tile width; see TmapIndex); tm_f0 / tm_f1: the field buffers
+    // the u maps describe.  The launcher narrows tmaps to the set of its tile
+    // width and sets tm_u to the map of prm.u (-1: per-thread loads).
+    const void* tmaps;
+    const void* tm_f0;
+    const void* tm_f1;
+    const void* tm_fw;    // the autotuner's scratch field buffer (map TM_UW), or null
+    int32_t tm_u;
 };
+
+// Tensor maps (CUtensorMap, 128 bytes each) of one tile width, all with the
+// tile's columns as the innermost box dimension: the field buffers as
+// [6][N][C] (box TE x N x 6), the element constants [G_COUNT][K] (box TE x 16),
+// the face constants as [4][16][K] (box TE x 15 x 4, or x 16 with the interior
+// penalty) and the metric rows of the face-constant table [FC_ROWS][K] (box
+// TE x 6, or TE x 15 with A^T); TM_UW: a field-shaped scratch buffer of the
+// autotuner (dgm_autotune), encoded while it times.
+enum TmapIndex {
+    TM_U0 = 0, TM_U1 = 1, TM_GEO = 2, TM_FC = 3, TM_FCS = 4, TM_GM = 5, TM_GMGA = 6, TM_UW = 7,
+    TMAP_COUNT = 8
+};
+constexpr int TMAP_BYTES = 128;
+// rows of the boxes (the stage kernel's shared-memory rows): element constants,
+// face constants per face (15, or 16 with the penalty) of the 16 per face of
+// the table, metric, A^T
+constexpr int TM_ROWS_EG = 16, TM_ROWS_FC = 15, TM_ROWS_FACE = 16, TM_ROWS_GM = 6, TM_ROWS_GA = 9;
+// set 0: tiles of 128 bytes per row (32 FP32 or 16 FP64 columns); set 1: 16 FP32 columns
+constexpr int TMAP_SETS = 2;
 
 // Rows per element of the precomputed face constants: 4 faces x 16, the
 // metric A^T A (6), A^T (9).

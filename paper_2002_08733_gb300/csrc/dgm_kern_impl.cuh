@@ -157,6 +157,16 @@ int launch_mode(const StageParams& prm, cudaStream_t st) {
     q.a_f = float(prm.a);
     q.b_f = float(prm.b);
     const bool i32 = !q.force_index64 && fits_32bit(q);
+    // phase-1 bulk copies: the plan's tensor-map set of this tile width (rows
+    // of 128 bytes, or 16 FP32 columns) and the map of this stage's input
+    q.tm_u = -1;
+    constexpr int kSet = kTC ? -1 : (kTE * int(sizeof(Real)) == 128 ? 0 : (sizeof(Real) == 4 && kTE == 16 ? 1 : -1));
+    if (kSet >= 0 && q.tmaps != nullptr && q.S == 1) {
+        q.tmaps = static_cast<const char*>(q.tmaps) + size_t(kSet) * TMAP_COUNT * TMAP_BYTES;
+        q.tm_u = q.u == q.tm_f0 ? TM_U0
+                 : q.u == q.tm_f1 ? TM_U1
+                 : (q.tm_fw != nullptr && q.u == q.tm_fw) ? TM_UW : -1;
+    }
     if (q.hs != nullptr) {   // interior penalty
         if constexpr (kSIP) {
             return i32 ? launch_ix<uint32_t, true>(q, grid, st) : launch_ix<int64_t, true>(q, grid, st);

@@ -46,6 +46,7 @@
 
 #include "dgm_internal.h"
 #include "dgm_ops_gen.cuh"
+#include "dgm_bulk.cuh"
 #include "dgm_tc.cuh"
 
 namespace dgm {
@@ -100,11 +101,12 @@ template <bool SIP> __host__ __device__ constexpr int nbs_rows() { return SIP ? 
 
 template <int P, typename R, int TE, bool TC = false, bool SIP = false>
 __host__ __device__ constexpr size_t stage_smem_bytes() {
-    // tensor-core variant: + an mbarrier and the tensor-memory base (the operator
-    // image lives in the neighbour-trace array, dead after phase 3)
+    // + an mbarrier (phase-1 bulk copies; the tensor-core variant's MMAs) and the
+    // tensor-memory base (the operator image lives in the neighbour-trace array,
+    // dead after phase 3)
     return sizeof(R) * size_t(TE) *
                (6 * nmodes(P) + 48 * nfmodes(P) + 4 * fgr<SIP>() + EG + GM + (SIP ? GA : 0) + nbs_rows<SIP>()) +
-           (TC ? size_t(32) : size_t(0));
+           size_t(32);
 }
 
 // Reference operators: straight-line code with literal coefficients generated
@@ -272,6 +274,9 @@ __device__ __forceinline__ void face_constants_ref(int f, const R (&ait)[9], R d
 // stage kernel, so the same bits.
 constexpr int FCF = FGR + 1;
 static_assert(4 * FCF + GM + GA == FC_ROWS, "precomputed face-constant rows");
+static_assert(EG == TM_ROWS_EG && FGR == TM_ROWS_FC && FCF == TM_ROWS_FACE && GM == TM_ROWS_GM &&
+                  GA == TM_ROWS_GA,
+              "bulk-copy boxes match the shared-memory rows");
 template <typename R, bool SIP>
 __global__ void face_consts_kernel(const StageParams prm, R* __restrict__ out) {
     const int64_t K = prm.K;
@@ -632,8 +637,9 @@ stage_kernel(const StageParams prm) {
     static_assert(!TC || (sizeof(R) == 4 && TE == 64 && (MODE == MODE_LSRK || MODE == MODE_RHS) &&
                           (NT / TE) % 2 == 0 && TcShape<P>::FITS),
                   "tensor-core variant: FP32, 64 columns, LSRK or right-hand side, even groups");
-    // tensor-core variant: mbarrier and tensor-memory base address after the
-    // tables; the operator image goes into the neighbour-trace array in phase 4
+    // mbarrier (phase-1 bulk copies; tensor-core variant: its MMAs) and the
+    // tensor-memory base address after the tables; the tensor-core variant's
+    // operator image goes into the neighbour-trace array in phase 4
     uint64_t* tc_bar = reinterpret_cast<uint64_t*>(
         (reinterpret_cast<uintptr_t>(nbs + nbs_rows<SIP>() * TE) + 7) & ~uintptr_t(7));
     uint32_t* tc_base = reinterpret_cast<uint32_t*>(tc_bar + 1);
@@ -671,7 +677,8 @@ stage_kernel(const StageParams prm) {
     // constants, and the face constants and metric that the plan precomputed
     // (face_consts_kernel), each thread's loads in flight together before its
     // shared-memory stores; every group requests the neighbour coefficients of
-    // its first phase-2 item, so that the global round trips of the tile overlap.
+    // its first two neighbour items and traces the first, so that the global
+    // round trips of the tile and the gathers overlap each other and work.
     constexpr int NOWN = 12, NNBR = 24;                 // phase-2 items
     R vn[N];                                            // neighbour coefficients (phase 2)
     auto nbr_item_active = [&](int comp) {
@@ -686,7 +693,55 @@ stage_kernel(const StageParams prm) {
             for (int l = 0; l < N; ++l) dst[l] = u[IX((ni % 6) * N + l) * C + ncol];
         }
     };
-    {
+    // neighbour item ni: the trace of the neighbour's coefficients v on its
+    // face (code & 3) into trN (zeros without a neighbour)
+    auto nbr_trace = [&](int ni, int32_t code, const R (&v)[N]) {
+        if (ni < NNBR && nbr_item_active(ni % 6)) {
+            const int nf = ni / 6, ncomp = ni % 6;
+            const bool has_nbr = code >= 0 && (code >> 2) < K;
+            if (code >= 0 && (code >> 2) >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
+            R acc[NF];
+            if (has_nbr) {
+                trace_any<P, R>(code & 3, v, acc);
+            } else {
+#pragma unroll
+                for (int m = 0; m < NF; ++m) acc[m] = R(0);
+            }
+            R* dst = trN + ((nf * 6 + ncomp) * NF) * TE + c;
+#pragma unroll
+            for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
+        }
+    };
+    // neighbour codes of this group's items of rounds 0 and 1 (the staged
+    // copies in nbs are not visible before the phase-1 barrier)
+    const int32_t code0 = (grp < NNBR && active) ? prm.nbr[IX(grp / 6) * K + e] : -1;
+    const int32_t code1 = (grp + NG < NNBR && active) ? prm.nbr[IX((grp + NG) / 6) * K + e] : -1;
+    R vn1[N];                                           // round-1 neighbour coefficients
+    // Tiled bulk copies where the plan has tensor maps for this tile (one column
+    // per element, aligned rows; tm_u >= 0): thread 0 issues four copies (the
+    // coefficients [6][N][TE], the element constants, the face constants, the
+    // metric and A^T) onto an mbarrier and waits for them itself, with a time
+    // limit, while every thread gathers and traces neighbour coefficients; the
+    // phase-1 barrier then publishes the tile.  Columns past the end arrive as
+    // zeros, which only inactive columns see.  Otherwise every thread loads
+    // and stores its share of rows.
+    constexpr bool BULK_OK = !TC && (TE * int(sizeof(R)) == 128 || (sizeof(R) == 4 && TE == 16));
+    const bool bulk = BULK_OK && prm.tm_u >= 0 && (tc::smem_addr(smem_raw) & 127u) == 0;
+    if (bulk) {
+        constexpr uint32_t BYTES = uint32_t(sizeof(R)) * TE * (6 * N + EG + 4 * FGRT + GM + (SIP ? GA : 0));
+        if (threadIdx.x == 0) {
+            tc::mbar_init(tc_bar, 1);
+            bulk::arrive_expect_tx(tc_bar, BYTES);
+            const char* tm = static_cast<const char*>(prm.tmaps);
+            const int x = int(tile_index(prm.tile_groups)) * TE;
+            bulk::load_3d(us, tm + prm.tm_u * TMAP_BYTES, x, 0, 0, tc_bar);
+            bulk::load_2d(eg, tm + TM_GEO * TMAP_BYTES, x, 0, tc_bar);
+            bulk::load_3d(fg, tm + (SIP ? TM_FCS : TM_FC) * TMAP_BYTES, x, 0, 0, tc_bar);
+            bulk::load_2d(gm, tm + (SIP ? TM_GMGA : TM_GM) * TMAP_BYTES, x, 4 * FCF, tc_bar);
+        }
+        request_nbr(grp, code0, vn);
+        request_nbr(grp + NG, code1, vn1);
+    } else {
         // rows q: [0, 6N) coefficients, then EG element constants, 4 FGRT face
         // constants, GM metric rows and (penalty) GA rows of A^T
         constexpr int Q0 = 6 * N, Q1 = Q0 + EG, Q2 = Q1 + 4 * FGRT, Q3 = Q2 + GM;
@@ -714,8 +769,6 @@ stage_kernel(const StageParams prm) {
             else if (q < Q3) gm[(q - Q2) * TE + c] = v;
             else ga[(q - Q3) * TE + c] = v;
         };
-        // neighbour code of this group's round-0 item, with the first batch
-        const int32_t code0 = (grp < NNBR && active) ? prm.nbr[IX(grp / 6) * K + e] : -1;
         R tmp[BATCH];
 #pragma unroll
         for (int i0 = 0; i0 < UR; i0 += BATCH) {
@@ -731,42 +784,51 @@ stage_kernel(const StageParams prm) {
                 if (i0 + i < UR && q < T1) store(q, tmp[i]);
             }
         }
+        request_nbr(grp + NG, code1, vn1);
     }
-    __syncthreads();
+    // Round 0 of the neighbour traces before the phase-1 barrier: it needs only
+    // registers and writes rows of trN that phase 1 does not touch, so its
+    // gathers and arithmetic overlap the copies and the wait for the slowest
+    // group.
+    nbr_trace(grp, code0, vn);
+#pragma unroll
+    for (int l = 0; l < N; ++l) vn[l] = vn1[l];
+    if (bulk) {
+        bool ok = true;
+        if (threadIdx.x == 0) ok = tc::mbar_wait(tc_bar, 0, 500000000ull);
+        if (!__syncthreads_and(ok)) {
+            // the copies did not complete in time: latch the status, give them a
+            // second bounded wait (the shared memory stays this CTA's until its
+            // last thread exits) and leave the tile untouched
+            if (threadIdx.x == 0) {
+                atomicOr(prm.status, int32_t(ST_TIMEOUT));
+                tc::mbar_wait(tc_bar, 0, 500000000ull);
+            }
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
 
     // ---- phase 2: traces ------------------------------------------------------
-    // Neighbour traces: item (face, component), one per group and round; the
-    // coefficients of round rr + 1 are requested before the arithmetic of
-    // round rr (those of round 0 in phase 1), so every gather overlaps work.
-    // Own traces: item (component, pair of faces), sharing one load of the
-    // component's coefficients between two faces, in the last rounds.
+    // Neighbour traces: item (face, component), one per group and round; round
+    // 0 ran in phase 1, and the coefficients of round rr + 1 are requested
+    // before the arithmetic of round rr (those of round 1 in phase 1), so every
+    // gather overlaps work.  Own traces: item (component, pair of faces),
+    // sharing one load of the component's coefficients between two faces, in
+    // the last rounds.
     {
         constexpr int ROUNDS = (NNBR + NG - 1) / NG;
         constexpr int OWN_ROUNDS = (NOWN + NG - 1) / NG;
-        // unrolled (two rounds at 12 groups) so that handing the prefetched
-        // coefficients to the next round is register renaming, not copies
+        // unrolled so that handing the prefetched coefficients to the next
+        // round is register renaming, not copies
 #pragma unroll
         for (int rr = 0; rr < ROUNDS; ++rr) {
             const int ni = grp + rr * NG;
             R vnx[N];
-            if (rr + 1 < ROUNDS && ni + NG < NNBR)
+            if (rr >= 1 && rr + 1 < ROUNDS && ni + NG < NNBR)
                 request_nbr(ni + NG, nbs[((ni + NG) / 6) * TE + c], vnx);
-            if (ni < NNBR && nbr_item_active(ni % 6)) {
-                const int nf = ni / 6, ncomp = ni % 6;
-                const int32_t code = nbs[nf * TE + c];
-                const bool has_nbr = code >= 0 && (code >> 2) < K;
-                if (code >= 0 && (code >> 2) >= K) atomicOr(prm.status, ST_BAD_NEIGHBOUR);
-                R acc[NF];
-                if (has_nbr) {
-                    trace_any<P, R>(code & 3, vn, acc);
-                } else {
-#pragma unroll
-                    for (int m = 0; m < NF; ++m) acc[m] = R(0);
-                }
-                R* dst = trN + ((nf * 6 + ncomp) * NF) * TE + c;
-#pragma unroll
-                for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
-            }
+            if (rr >= 1) nbr_trace(ni, ni < NNBR ? nbs[(ni / 6) * TE + c] : -1, vn);
             const int oi = grp + (rr - (ROUNDS - OWN_ROUNDS)) * NG;   // own item of this round
             if (rr >= ROUNDS - OWN_ROUNDS && oi < NOWN && nbr_item_active(oi % 6)) {
                 const int ocomp = oi % 6, fp = oi / 6;
@@ -786,8 +848,10 @@ stage_kernel(const StageParams prm) {
                     for (int m = 0; m < NF; ++m) dst[m * TE] = acc[m];
                 }
             }
+            if (rr >= 1) {
 #pragma unroll
-            for (int l = 0; l < N; ++l) vn[l] = vnx[l];
+                for (int l = 0; l < N; ++l) vn[l] = vnx[l];
+            }
         }
     }
     __syncthreads();

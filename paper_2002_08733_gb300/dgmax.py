@@ -91,6 +91,8 @@ _SIGS = {
     "dgm_autotune_info": [_P, _P, _P],
     "dgm_set_variant": [_P, ctypes.c_int32],
     "dgm_set_index64": [_P, ctypes.c_int32],
+    "dgm_set_tile_loads": [_P, ctypes.c_int32],
+    "dgm_get_tile_loads": [_P, ctypes.c_void_p],
     "dgm_set_tile_groups": [_P, ctypes.c_int32],
     "dgm_get_tile_groups": [_P, ctypes.c_void_p],
     "dgm_adjoint_workspace": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
@@ -456,6 +458,17 @@ class Solver(Plan):
     def set_index64(self, force=True):
         """Force 64-bit index arithmetic in the stage kernels (default: automatic)."""
         _check(_lib.dgm_set_index64(self.handle, int(bool(force))))
+
+    def set_tile_loads(self, per_thread=True):
+        """Force per-thread tile loads in phase 1 of the stage kernels (default:
+        tiled bulk copies where the plan allows them)."""
+        _check(_lib.dgm_set_tile_loads(self.handle, int(bool(per_thread))))
+
+    def bulk_tile_loads(self):
+        """True when the next stages move their tiles with tiled bulk copies."""
+        b = ctypes.c_int32()
+        _check(_lib.dgm_get_tile_loads(self.handle, ctypes.byref(b)))
+        return bool(b.value)
 
     def set_materials(self, eps, mu):
         eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (self.K,)))

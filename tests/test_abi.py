@@ -241,3 +241,17 @@ def test_interior_penalty_plan_sizes_and_limits(lib):
         with pytest.raises(D.DgmError):
             D.Plan(xyz, tets, 1.0, 1.0, 2, "fp64", args.pop("flux"), args.pop("integrator"), 1e-3,
                    **args)
+
+
+def test_tile_load_choice_is_validated(lib):
+    """dgm_set_tile_loads takes 0 (bulk copies where allowed) or 1 (per-thread
+    loads); an unbound plan reports no bulk copies."""
+    from paper_2002_08733_gb300 import dgmax as D
+    xyz, tets = W.kuhn_mesh(4)
+    pl = D.Plan(xyz, tets, 1.0, 1.0, 2, "fp32", "upwind", "lsrk4", 1e-3)
+    bulk = ctypes.c_int32(7)
+    assert lib.dgm_get_tile_loads(pl.handle, ctypes.byref(bulk)) == 0 and bulk.value == 0
+    assert lib.dgm_set_tile_loads(pl.handle, 1) == 0
+    assert lib.dgm_set_tile_loads(pl.handle, 0) == 0
+    assert lib.dgm_set_tile_loads(pl.handle, 2) == 1          # DGM_EINVAL
+    assert lib.dgm_get_tile_loads(pl.handle, None) == 1

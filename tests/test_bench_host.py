@@ -83,12 +83,15 @@ def test_profiled_traffic_matches_shape_and_order(tmp_path):
     # the committed summary has lines for the orders the autotuner picks
     path = os.path.join(ROOT, "profiles", bench.TRAFFIC_PROFILE)
     for groups in (6, 12):
-        t = bench.profiled_traffic(path, 0, groups, 196608)
+        t = bench.profiled_traffic(path, 0, groups, 196608, "bulk")
         assert t is not None and 0.9 < t / 374341632 < 1.3
     f = tmp_path / "p.md"
-    f.write_text("traffic_bytes_per_element_stage variant=0 tile_groups=6: 1922\n"
-                 "traffic_bytes_per_element_stage variant=1 tile_groups=6: 2000\n")
+    f.write_text("traffic_bytes_per_element_stage variant=0 tile_groups=6 loads=bulk: 1922\n"
+                 "traffic_bytes_per_element_stage variant=0 tile_groups=6 loads=per_thread: 1950\n"
+                 "traffic_bytes_per_element_stage variant=1 tile_groups=6 loads=bulk: 2000\n")
     assert bench.profiled_traffic(str(f), 0, 6, 10) == 19220
+    assert bench.profiled_traffic(str(f), 0, 6, 10, "per_thread") == 19500
     assert bench.profiled_traffic(str(f), 1, 6, 10) == 20000
+    assert bench.profiled_traffic(str(f), 1, 6, 10, "per_thread") is None
     assert bench.profiled_traffic(str(f), 0, 3, 10) is None
     assert bench.profiled_traffic(str(tmp_path / "missing.md"), 0, 6, 10) is None

@@ -45,11 +45,13 @@ def test_lsrk4_trajectory(D, prec, tol):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("S", [1, 2, 3])
 def test_lsrk4_tile_load_paths(D, prec, tol, S):
-    """The stage kernel stages its tile with per-thread loads of column rows;
-    with C = 162 S columns a row starts on a 16-byte boundary for some S
+    """With C = 162 S columns a row starts on a 16-byte boundary for some S
     (FP32: S = 2; FP64: every S) and not for others (FP32: S = 1, 3), and the
-    last tile is ragged.  Six LSRK4 steps with PML auxiliaries and a source
-    in column 0 match the oracle for each S."""
+    last tile is ragged.  Phase 1 moves the tile with tiled bulk copies only
+    for FP64 at S = 1 (one column per element, aligned rows); every other case
+    here takes per-thread loads (tests/test_gpu_bulk.py compares the two
+    paths).  Six LSRK4 steps with PML auxiliaries and a source in column 0
+    match the oracle for each S."""
     xyz, tets = W.kuhn_mesh(3, (-1, -1, -1), (1, 1, 1), jitter=0.1, seed=23)
     K, p = len(tets), 2
     pml = dict(lo=(-0.5,) * 3, hi=(0.5,) * 3, thickness=0.5, sigma_max=20.0, order=2)
