@@ -729,6 +729,9 @@ stage_kernel(const StageParams prm) {
     const bool bulk = BULK_OK && prm.tm_u >= 0 && (tc::smem_addr(smem_raw) & 127u) == 0;
     if (bulk) {
         constexpr uint32_t BYTES = uint32_t(sizeof(R)) * TE * (6 * N + EG + 4 * FGRT + GM + (SIP ? GA : 0));
+        // every box dimension within the copy's limit of 256, the byte count
+        // within the mbarrier's transaction count (2^20 - 1)
+        static_assert(!BULK_OK || (TE <= 256 && N <= 256 && BYTES < (1u << 20)), "bulk-copy boxes");
         if (threadIdx.x == 0) {
             tc::mbar_init(tc_bar, 1);
             bulk::arrive_expect_tx(tc_bar, BYTES);
