@@ -576,7 +576,9 @@ static int build_tmaps(dgm_plan* P) {
     P->tmaps_ok = false;
     const int rs = P->kt->real_size;
     const int64_t K = P->mesh.K;
-    if (P->opt.n_columns != 1 || K <= 0 || (K * rs) % 16 != 0 || K >= (int64_t(1) << 31)) return DGM_OK;
+    // (mixed-order plans run their own kernel on fields of 3 (N + N_H) rows)
+    if (P->mixed || P->opt.n_columns != 1 || K <= 0 || (K * rs) % 16 != 0 || K >= (int64_t(1) << 31))
+        return DGM_OK;
     if (tmap_encoder() == nullptr) return DGM_OK;
     P->tmap_host.assign(size_t(TMAP_SETS) * TMAP_COUNT, CUtensorMap{});
     for (int b = 0; b < 2; ++b)
